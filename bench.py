@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Benchmark of the limited-neighbourhood search (arXiv 2107.09801, Algorithm 1).
+
+Metric: flip-evals/s (neighbours scored per second, the paper's NSE/s) at
+L = 2^17 - 1 over 1024 independent walks (seeds 0..1023, alpha 4/13,
+N_lmt 6912), batched form; the plain form (one walk per launch, one thread per
+neighbour, host-side selection) is measured beside it.  One step = one pass of
+the whole hot path (score window, select, exact re-check, decide, O(L) update)
+for every walk of the batch.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0.
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import hashlib
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import psl_workloads as W  # noqa: E402
+
+METRIC = "flip evals/s at L=2^17−1 (batched vs plain); p50/p99 serving latency"
+UNIT = "flip-evals/s"
+PAPER_A100_L131071 = 638043  # Table 4 of the paper: one walk on an A100 SXM4 (context only)
+SM_COUNT_GB300 = 152
+LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--walks", type=int, default=1024)
+    ap.add_argument("--plain-steps", type=int, default=4)
+    ap.add_argument("--cpu-sample-s", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks during the timed region
+# ------------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.f.read())) if len(r) >= 9]
+        self.f.close()
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() in ("active", "1"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+# the oracle on the host cores (reference arm and cpu_baseline)
+# ------------------------------------------------------------------------------------------------
+def oracle_rate(L: int, n_lmt: int, alpha: int, seconds: float, threads: int | None = None):
+    """Flip-evals/s of the oracle's neighbour evaluation (exact F and PSL of each
+    neighbour, Eq. 2-4 through the one-element flip) on `threads` host threads, each on
+    its own walk, over a bounded sample of window positions sized to about `seconds`."""
+    import numpy as np
+
+    import oracle as O
+
+    threads = threads or os.cpu_count() or 1
+    walks = [None] * threads
+
+    def init(r):
+        walks[r] = O.Walk(O.WalkParams(L=L, seed=r, alpha1=alpha, alpha2=13, n_lmt=n_lmt))
+
+    ts = [threading.Thread(target=init, args=(r,)) for r in range(threads)]
+    [t.start() for t in ts]
+    [t.join() for t in ts]
+    # calibrate on one neighbour, then size the per-thread sample
+    w0 = walks[0]
+    t0 = time.perf_counter()
+    O.eval_neighbours(w0.s, w0.C, alpha, [1])
+    per = max(time.perf_counter() - t0, 1e-4)
+    n_per = int(max(1, min(n_lmt, seconds / per)))
+    counts = [0] * threads
+
+    def work(r):
+        w = walks[r]
+        start = O.splitmix64(w.p.seed, w.rng_ctr) % L
+        js = [(start + i) % L for i in range(1, n_per + 1)]
+        O.eval_neighbours(w.s, w.C, alpha, js)
+        counts[r] = len(js)
+
+    ts = [threading.Thread(target=work, args=(r,)) for r in range(threads)]
+    t0 = time.perf_counter()
+    [t.start() for t in ts]
+    [t.join() for t in ts]
+    dt = time.perf_counter() - t0
+    return sum(counts) / dt, threads, n_per, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    L, N = 131071, W.N_LMT
+    threads = os.cpu_count() or 1
+    # each step: every host thread evaluates a bounded slice of its walk's window
+    per_step_s = max(0.5, min(6.0, 150.0 / max(1, args.steps + args.warmup)))
+    vals = []
+    for s in range(args.warmup + args.steps):
+        v, cores, n_per, dt = oracle_rate(L, N, 4, per_step_s, threads)
+        if s >= args.warmup:
+            vals.append((v, dt, n_per))
+    value = statistics.median(v for v, _, _ in vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.median(d for _, d, _ in vals),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i384 exact (oracle)",
+            "data": "synthetic", "config": {"workload": "L131071_x1024", "L": L, "n_lmt": N, "alpha": "4/13"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"per step: {cores} threads x {vals[0][2]} window neighbours of their own "
+                                       f"L=131071 walk (exact F and PSL each)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------------------
+# our arm
+# ------------------------------------------------------------------------------------------------
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    for fn in ("psl_kernels.cu", "psl_internal.h"):
+        with open(os.path.join(ROOT, "paper_2107_09801_gb300", "csrc", fn), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def stored_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from an ncu capture, only if taken on the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        d = json.load(open(p))
+        rec = d[kernel][workload]
+        if rec.get("source_hash") == kernel_source_hash():
+            return rec["bytes_per_launch"]
+    except Exception:
+        pass
+    return None
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2107_09801_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+
+    wl = W.batch_131071(walks=args.walks)
+    specs = [W.WalkSpec(L=s.L, seed=s.seed + rank * args.walks, alpha1=s.alpha1, alpha2=s.alpha2, budget=s.budget)
+             for s in wl.walks]
+    L, N = specs[0].L, specs[0].N
+    assert args.warmup + args.steps <= specs[0].budget
+    need = sum(P.psl_walk_bytes(s.L, s.n_lmt, 0) for s in specs)
+    arena = torch.empty(int(need * 1.1) + (64 << 20), dtype=torch.uint8, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    out = {}
+    with P.Context(arena_tensor=arena, stream=stream, max_walks=len(specs), device=local) as ctx:
+        ids = [ctx.submit(s.L, s.seed, s.alpha1, s.alpha2, s.budget) for s in specs]
+        ctx.step(args.warmup)   # admission, initialisation and warm-up steps
+        barrier()
+        clk = ClockSampler(local)
+        clk.start()
+        ctx.profile(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.step(args.steps)
+        e1.record(stream)
+        barrier()
+        prof = ctx.profile_read()
+        ctx.profile(False)
+        clocks = clk.stop()
+        ms = e0.elapsed_time(e1)
+        st = [ctx.poll(i) for i in ids[:4]]
+        assert all(s["moves"] == args.warmup + args.steps for s in st)
+    t = torch.tensor([ms], device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    flip_evals_rank = len(specs) * N * args.steps
+    value = world * flip_evals_rank / (ms_max / 1000.0)
+
+    # roofline of the dominant kernel (the neighbourhood score), live durations
+    n_hot, hot_ms = prof.get("hot", (0, 0.0))
+    hot_avg_ms = hot_ms / max(n_hot, 1)
+    ops_per_launch = len(specs) * N * 2 * (L - 1)        # 2 lane-ops per (j, k) term, (L-1) terms
+    achieved = ops_per_launch / (hot_avg_ms / 1000.0)
+    mhz = clocks.get("sm_mhz") or 2070.0
+    peak = SM_COUNT_GB300 * LANES_PER_SM * mhz * 1e6
+    kernels = {k: {"launches": n, "avg_ms": (ms_ / n if n else 0.0)} for k, (n, ms_) in prof.items() if n}
+    launches = sum(n for k, (n, _) in prof.items() if k != "init")
+
+    # plain form: one walk per launch, one thread per neighbour, host-side selection
+    plain = None
+    if not args.no_plain and rank == 0:
+        with P.Context(form="plain", arena_bytes=P.psl_walk_bytes(L, N, 0) + (16 << 20), stream=stream,
+                       max_walks=2, device=local) as pc:
+            pid = pc.submit(L, 0, 4, 13, 2000)
+            pc.step(1)
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            pc.step(args.plain_steps)
+            torch.cuda.synchronize(dev)
+            dt = time.perf_counter() - t0
+            plain = {"value": N * args.plain_steps / dt, "walks": 1, "steps": args.plain_steps,
+                     "ms_per_step": 1000 * dt / args.plain_steps}
+
+    # end to end through the public API: submit from the host, run, read every walk's
+    # status and best sequence back into host memory
+    e2e = None
+    if not args.no_e2e:
+        barrier()
+        t0 = time.perf_counter()
+        with P.Context(arena_tensor=arena, stream=stream, max_walks=len(specs), device=local) as ctx:
+            ids = [ctx.submit(s.L, s.seed, s.alpha1, s.alpha2, s.budget) for s in specs]
+            ctx.step(args.steps)
+            psl_sum = 0
+            for i in ids:
+                p, seq = ctx.best(i)
+                psl_sum += p
+        torch.cuda.synchronize(dev)
+        dt = time.perf_counter() - t0
+        td = torch.tensor([dt], device=dev)
+        if world > 1:
+            dist.all_reduce(td, op=dist.ReduceOp.MAX)
+        hdr_bytes = 512
+        e2e = {"value": world * flip_evals_rank / float(td.item()), "unit": UNIT,
+               "h2d_bytes_per_step": (len(specs) * (hdr_bytes + 64)) / args.steps,
+               "d2h_bytes_per_step": (len(specs) * hdr_bytes * args.steps + len(specs) * L) / args.steps,
+               "includes": "submit, walk initialisation, steps, status and best-sequence readback"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32 (exact i384 decisions)",
+                "data": "synthetic",
+                "config": {"workload": wl.name, "L": L, "walks_per_gpu": len(specs), "n_lmt": N, "alpha": "4/13",
+                           "ls_lmt": W.LS_LMT, "flip_lmt": W.FLIP_LMT, "form": "batched",
+                           "l2": "inputs larger than L2 (walk state %.1f GB per GPU)" % (need / 1e9)},
+                "roofline": {"bound": "alu", "kernel": "k_hot_batched", "achieved": achieved / 1e12,
+                             "peak": peak / 1e12, "unit": "Tops/s", "frac": achieved / peak,
+                             "traffic": stored_traffic("k_hot_batched", wl.name),
+                             "peak_basis": f"{SM_COUNT_GB300} SMs x {LANES_PER_SM} lanes x {mhz:.0f} MHz "
+                                           "(median SM clock sampled in the timed region)",
+                             "ops_basis": "2 lane-ops per (neighbour, shift) term, (L-1) terms per flip-eval"},
+                "clocks": clocks, "gpu_launches": launches, "kernels": kernels,
+                "plain": plain,
+                "batched_over_plain": (value / world) / plain["value"] if plain else None,
+                "paper_context": {"A100_one_walk_flip_evals_per_s_L131071": PAPER_A100_L131071},
+                "e2e": e2e}
+        if not args.no_cpu_baseline:
+            v, cores, n_per, dt = oracle_rate(L, N, 4, args.cpu_sample_s)
+            line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                    "sample": f"{cores} threads x {n_per} window neighbours of their own L=131071 "
+                                              f"walk, exact F and PSL each ({dt:.1f} s)"}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

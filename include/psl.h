@@ -1,0 +1,218 @@
+/*
+ * psl.h -- C ABI of the GB300 library for the limited-neighbourhood search of
+ * Boskovic and Brest, "Two-phase Optimization of Binary Sequences with Low Peak
+ * Sidelobe Level Value" (arXiv 2107.09801).
+ *
+ * What the library computes (paper notation, 0-based indices):
+ *   a sequence s_0..s_{L-1}, s_i in {+1,-1}                          (Eq. 1)
+ *   C_k = sum_{i=0}^{L-1-k} s_i s_{i+k}, k = 0..L-1                   (Eq. 2)
+ *   PSL = max_{k=1..L-1} |C_k|                                        (Eq. 3, range read as 1..L-1)
+ *   F_alpha = sum_{k=1}^{L-1} |C_k|^alpha                             (Eq. 4)
+ * and runs Algorithm 1 ("Search algorithm"): every step scores a window of
+ * N = min(N_lmt, L) single-flip neighbours j = (start + i) % L, i = 1..N, with
+ * start = Rand() % L, through the one-element flip update of Sec. 3
+ * (C'_k = C_k - 2 s_j (s_{j+k} + s_{j-k}), absent partners counting 0), moves to
+ * the first neighbour of minimum F in scan order (a forced move), keeps the first
+ * neighbour of minimum PSL ever evaluated as the best solution, and after more
+ * than LS_lmt non-improving steps restarts from local_best with FLIP_lmt random
+ * flips while toggling alpha between alpha1 and alpha2.
+ *
+ * Decisions are exact: F is held as an exact 384-bit integer and every
+ * comparison of Algorithm 1 is made on exact values.  The GPU ranks neighbours
+ * with an FP32 score whose rounding error is bounded rigorously, and re-scores
+ * exactly every neighbour that the bound cannot exclude (plus the FP32 top-k).
+ * Results of a walk depend only on its parameters, never on which other walks
+ * share the GPU.
+ *
+ * Readings where the paper is silent: Rand is SplitMix64 seeded per walk (draw
+ * order: ceil(L/64) draws for the start sequence, bit b of draw q giving
+ * s_{64q+b} with bit 1 meaning -1; one draw per step for start; at a switch,
+ * draws % L until min(FLIP_lmt, L) distinct flip positions are found); psl_best,
+ * solution_best and local_best start at the start sequence; local_best is kept
+ * at a switch; the budget counts steps (each step is one move); alpha is an
+ * integer in 1..16.
+ *
+ * Conventions: functions return PSL_OK (0) or a count >= 0 on success and a
+ * negative PSL_E* code on failure.  The library owns all device memory it
+ * allocates (or the caller-provided arena) and every device buffer inside it;
+ * the caller owns every host buffer passed in.  A context is used by one host
+ * thread at a time.
+ */
+#ifndef PSL_H
+#define PSL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PSL_API __attribute__((visibility("default")))
+#else
+#define PSL_API
+#endif
+
+#define PSL_OK 0
+#define PSL_EINVAL (-1)   /* an argument is outside its documented range      */
+#define PSL_ENOMEM (-2)   /* the walk can never fit the arena / allocation failed */
+#define PSL_ENOENT (-3)   /* unknown walk id                                   */
+#define PSL_EBUSY (-4)    /* the walk is still queued or running               */
+#define PSL_ETIMEOUT (-5) /* a bounded device wait expired                     */
+#define PSL_ECUDA (-6)    /* a CUDA runtime call failed (see psl_last_error)   */
+#define PSL_ESTATE (-7)   /* the walk is in an error state                     */
+
+#define PSL_FORM_BATCHED 0 /* all running walks advance together; persistent-style batched kernels */
+#define PSL_FORM_PLAIN 1   /* one walk per launch, one thread per neighbour, host-side selection   */
+
+#define PSL_QUEUED 0
+#define PSL_RUNNING 1
+#define PSL_DONE 2
+#define PSL_ERROR 3
+
+typedef struct psl_ctx psl_ctx;
+
+/* Library configuration.  Fill with psl_config_default() and override. */
+typedef struct {
+  int32_t n_lmt;            /* default N_lmt (Sec. 4.1: 6912)                         */
+  int32_t ls_lmt;           /* default LS_lmt (Sec. 4.1: 2000)                        */
+  int32_t flip_lmt;         /* default FLIP_lmt (Sec. 4.1: 10)                        */
+  int32_t device;           /* CUDA device ordinal                                    */
+  uint64_t arena_bytes;     /* device arena size in bytes; 0 = library default       */
+  void *arena;              /* optional caller-owned device buffer of arena_bytes    */
+  void *stream;             /* cudaStream_t for all work; NULL = library-owned stream */
+  int32_t form;             /* PSL_FORM_BATCHED or PSL_FORM_PLAIN                     */
+  int32_t max_walks;        /* number of walk slots                                   */
+  int32_t hot_tile_sb;      /* k-tile of the batched kernel, super-blocks of 30 k; 0 = auto */
+  int32_t steps_per_graph;  /* steps captured per CUDA graph launch; 0 = plain launches */
+} psl_config;
+
+/* Per-walk parameters of psl_submit_ex.  n_lmt, flip_lmt <= 0 and ls_lmt < 0 take
+ * the context default; topk <= 0 means 1. */
+typedef struct {
+  uint32_t L;               /* sequence length, 2 <= L <= 2^20 - 1                     */
+  uint64_t seed;            /* walk seed of Rand                                      */
+  int32_t alpha1, alpha2;   /* integer exponents of Eq. 4 for the two phases, 1..16   */
+  uint64_t budget;          /* number of steps (moves), >= 1                          */
+  int32_t n_lmt, ls_lmt, flip_lmt;
+  int32_t topk;             /* FP32-ranked neighbours re-scored exactly besides the certified set (1..16) */
+  const int8_t *init_seq;   /* optional host array of L values +-1 replacing Rand(L, SEED); copied */
+  uint32_t trace_cap;       /* per-step records kept on the device (0 = none)        */
+} psl_walk_params;
+
+/* Snapshot of one walk (psl_poll). */
+typedef struct {
+  int32_t state;            /* PSL_QUEUED / PSL_RUNNING / PSL_DONE / PSL_ERROR        */
+  int32_t error;            /* PSL_E* code when state == PSL_ERROR                    */
+  uint32_t L;
+  uint32_t alpha;           /* exponent of the current phase                          */
+  uint64_t moves;           /* steps completed                                        */
+  uint64_t flip_evals;      /* neighbours scored (N per step)                         */
+  uint64_t switches;        /* phase switches                                         */
+  uint64_t rechecks;        /* neighbours re-scored exactly                           */
+  int32_t psl;              /* PSL of the current pivot                               */
+  int32_t psl_best;         /* best PSL over every evaluated neighbour                */
+  uint32_t unimproved;      /* counter of Alg. 1                                      */
+  uint32_t pad;
+  double F;                 /* F_alpha(pivot), correctly rounded from the exact value */
+  double value_local;       /* value_local of Alg. 1, correctly rounded               */
+  double t_submit, t_start, t_done; /* host monotonic seconds                         */
+} psl_status;
+
+/* Per-step record (psl_trace).  value_exact holds the exact F of the chosen
+ * neighbour as 12 little-endian 32-bit limbs of a two's-complement integer. */
+typedef struct {
+  uint64_t step;
+  uint32_t start, kstar, alpha, unimproved;
+  int32_t psl, psl_best, win_psl;
+  uint32_t win_psl_j, flags, nflip, ncand;
+  float score_kstar, score_min, bound;
+  uint32_t pad;
+  double value_step;
+  uint32_t value_exact[12];
+} psl_trace_rec;
+
+/* Full state of one walk for decision replay (psl_export_state). */
+typedef struct {
+  uint32_t L, N, alpha, unimproved;
+  int32_t psl, psl_best, psl_local;
+  uint32_t start;           /* window start of the next step                           */
+  uint64_t rng_ctr, moves;
+  uint32_t F[12], value_local[12];  /* exact, two's complement, little-endian limbs    */
+  int32_t state;
+  uint32_t pad;
+} psl_walk_state;
+
+/* Fills *cfg with defaults: N_lmt 6912, LS_lmt 2000, FLIP_lmt 10 (Sec. 4.1),
+ * device 0, library arena, library stream, batched form, 4096 slots. */
+PSL_API void psl_config_default(psl_config *cfg);
+
+/* Creates a context on cfg->device.  Errors: PSL_EINVAL (bad field),
+ * PSL_ECUDA / PSL_ENOMEM (device or arena unavailable). */
+PSL_API int psl_init(const psl_config *cfg, psl_ctx **out);
+
+/* Queues a walk of Algorithm 1 with the context's N_lmt / LS_lmt / FLIP_lmt.
+ * alpha1, alpha2 must be integers in 1..16; budget >= 1 steps.  Returns the walk
+ * id (>= 0) or PSL_EINVAL / PSL_ENOMEM (the walk can never fit the arena). */
+PSL_API int64_t psl_submit(psl_ctx *ctx, uint32_t L, uint64_t seed, double alpha1, double alpha2, uint64_t budget);
+
+/* As psl_submit with every per-walk field of psl_walk_params. */
+PSL_API int64_t psl_submit_ex(psl_ctx *ctx, const psl_walk_params *p);
+
+/* Admits queued walks while the arena has room, then advances every running walk
+ * by up to max_moves steps (walks stop at their budget).  Blocks until the work
+ * is done.  Returns the number of walks still queued or running, or a PSL_E* code. */
+PSL_API int psl_step(psl_ctx *ctx, uint32_t max_moves);
+
+/* Status of a walk as of the end of the last psl_step.  PSL_ENOENT if unknown. */
+PSL_API int psl_poll(psl_ctx *ctx, int64_t id, psl_status *out);
+
+/* Best sequence found so far (solution_best of Alg. 1): *psl receives its PSL and
+ * seq_pm1[0..L-1] its values +-1; cap must be >= L.  PSL_EBUSY while queued. */
+PSL_API int psl_best(psl_ctx *ctx, int64_t id, int32_t *psl, int8_t *seq_pm1, size_t cap);
+
+/* Frees the walk's slot and device memory.  Running walks are cancelled. */
+PSL_API int psl_release(psl_ctx *ctx, int64_t id);
+
+/* Copies the walk's state (pivot, local_best, solution_best as +-1 arrays of cap >= L
+ * values each, any of them may be NULL; C_0..C_{L-1} if C != NULL). */
+PSL_API int psl_export_state(psl_ctx *ctx, int64_t id, psl_walk_state *st, int8_t *pivot, int8_t *local_best,
+                     int8_t *sol_best, int32_t *C, size_t cap);
+
+/* Copies up to cap per-step records; returns the number copied. */
+PSL_API int psl_trace(psl_ctx *ctx, int64_t id, psl_trace_rec *out, size_t cap);
+
+/* Aperiodic autocorrelation (Eq. 2) of nseq sequences given as +-1 host arrays
+ * (row-major nseq x L) into host C (nseq x L), computed on the device by the same
+ * bit-packed popcount kernel that initialises walks.  PSL_EINVAL on bad sizes. */
+PSL_API int psl_autocorr(psl_ctx *ctx, const int8_t *seq_pm1, uint32_t nseq, uint32_t L, int32_t *C);
+
+/* Device bytes a walk of length L with window n_lmt and trace_cap records needs. */
+PSL_API uint64_t psl_walk_bytes(uint32_t L, int32_t n_lmt, uint32_t trace_cap);
+
+/* Device time of the library's kernels, accumulated while profiling is enabled. */
+typedef struct {
+  char name[24];            /* kernel family: hot, select, recheck, decide, apply, hot_plain, init */
+  uint64_t launches;
+  double total_ms;          /* sum of CUDA-event durations measured on the context's stream */
+} psl_kernel_time;
+
+/* Enables (1) or disables (0) CUDA-event timing of every kernel launch of psl_step
+ * (launches captured in CUDA graphs are timed as one unit under "graph").
+ * Enabling resets the totals. */
+PSL_API int psl_profile(psl_ctx *ctx, int enable);
+
+/* Copies up to cap per-kernel totals; returns the number of kernel families. */
+PSL_API int psl_profile_read(psl_ctx *ctx, psl_kernel_time *out, size_t cap);
+
+/* Destroys the context and frees its device memory.  NULL is ignored. */
+PSL_API void psl_shutdown(psl_ctx *ctx);
+
+/* Message of the last error of this context (or of the last failed psl_init). */
+PSL_API const char *psl_last_error(psl_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PSL_H */

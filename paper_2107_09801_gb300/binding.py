@@ -1,0 +1,299 @@
+"""ctypes binding of include/psl.h.  Argument marshalling only: the search itself runs
+in libpsl.so.  Function names mirror the C ABI; ``Context`` bundles them."""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = os.path.join(_HERE, "_build", "libpsl.so")
+
+PSL_OK, PSL_EINVAL, PSL_ENOMEM, PSL_ENOENT, PSL_EBUSY, PSL_ETIMEOUT, PSL_ECUDA, PSL_ESTATE = 0, -1, -2, -3, -4, -5, -6, -7
+PSL_FORM_BATCHED, PSL_FORM_PLAIN = 0, 1
+PSL_QUEUED, PSL_RUNNING, PSL_DONE, PSL_ERROR = 0, 1, 2, 3
+WIDE = 12
+
+
+class PslError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"psl error {code}: {msg}")
+        self.code = code
+
+
+class psl_config(ct.Structure):
+    _fields_ = [("n_lmt", ct.c_int32), ("ls_lmt", ct.c_int32), ("flip_lmt", ct.c_int32), ("device", ct.c_int32),
+                ("arena_bytes", ct.c_uint64), ("arena", ct.c_void_p), ("stream", ct.c_void_p), ("form", ct.c_int32),
+                ("max_walks", ct.c_int32), ("hot_tile_sb", ct.c_int32), ("steps_per_graph", ct.c_int32)]
+
+
+class psl_walk_params(ct.Structure):
+    _fields_ = [("L", ct.c_uint32), ("seed", ct.c_uint64), ("alpha1", ct.c_int32), ("alpha2", ct.c_int32),
+                ("budget", ct.c_uint64), ("n_lmt", ct.c_int32), ("ls_lmt", ct.c_int32), ("flip_lmt", ct.c_int32),
+                ("topk", ct.c_int32), ("init_seq", ct.c_void_p), ("trace_cap", ct.c_uint32)]
+
+
+class psl_status(ct.Structure):
+    _fields_ = [("state", ct.c_int32), ("error", ct.c_int32), ("L", ct.c_uint32), ("alpha", ct.c_uint32),
+                ("moves", ct.c_uint64), ("flip_evals", ct.c_uint64), ("switches", ct.c_uint64),
+                ("rechecks", ct.c_uint64), ("psl", ct.c_int32), ("psl_best", ct.c_int32),
+                ("unimproved", ct.c_uint32), ("pad", ct.c_uint32), ("F", ct.c_double), ("value_local", ct.c_double),
+                ("t_submit", ct.c_double), ("t_start", ct.c_double), ("t_done", ct.c_double)]
+
+
+class psl_walk_state(ct.Structure):
+    _fields_ = [("L", ct.c_uint32), ("N", ct.c_uint32), ("alpha", ct.c_uint32), ("unimproved", ct.c_uint32),
+                ("psl", ct.c_int32), ("psl_best", ct.c_int32), ("psl_local", ct.c_int32), ("start", ct.c_uint32),
+                ("rng_ctr", ct.c_uint64), ("moves", ct.c_uint64), ("F", ct.c_uint32 * WIDE),
+                ("value_local", ct.c_uint32 * WIDE), ("state", ct.c_int32), ("pad", ct.c_uint32)]
+
+
+class psl_kernel_time(ct.Structure):
+    _fields_ = [("name", ct.c_char * 24), ("launches", ct.c_uint64), ("total_ms", ct.c_double)]
+
+
+TRACE_DTYPE = np.dtype([("step", "<u8"), ("start", "<u4"), ("kstar", "<u4"), ("alpha", "<u4"), ("unimproved", "<u4"),
+                        ("psl", "<i4"), ("psl_best", "<i4"), ("win_psl", "<i4"), ("win_psl_j", "<u4"),
+                        ("flags", "<u4"), ("nflip", "<u4"), ("ncand", "<u4"), ("score_kstar", "<f4"),
+                        ("score_min", "<f4"), ("bound", "<f4"), ("pad", "<u4"), ("value_step", "<f8"),
+                        ("value_exact", "<u4", (WIDE,))])
+
+EXPORTED = ["psl_config_default", "psl_init", "psl_submit", "psl_submit_ex", "psl_step", "psl_poll", "psl_best",
+            "psl_release", "psl_export_state", "psl_trace", "psl_autocorr", "psl_walk_bytes", "psl_shutdown",
+            "psl_last_error", "psl_profile", "psl_profile_read"]
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _LIB
+
+
+def lib():
+    """Loads libpsl.so; raises if it has not been built (no fallback exists)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(_LIB):
+            raise ImportError(f"{_LIB} is missing: build it with paper_2107_09801_gb300.build.build() "
+                              "(the search has no CPU fallback)")
+        L = ct.CDLL(_LIB)
+        P = ct.c_void_p
+        sig = {
+            "psl_config_default": (None, [ct.POINTER(psl_config)]),
+            "psl_init": (ct.c_int, [ct.POINTER(psl_config), ct.POINTER(P)]),
+            "psl_submit": (ct.c_int64, [P, ct.c_uint32, ct.c_uint64, ct.c_double, ct.c_double, ct.c_uint64]),
+            "psl_submit_ex": (ct.c_int64, [P, ct.POINTER(psl_walk_params)]),
+            "psl_step": (ct.c_int, [P, ct.c_uint32]),
+            "psl_poll": (ct.c_int, [P, ct.c_int64, ct.POINTER(psl_status)]),
+            "psl_best": (ct.c_int, [P, ct.c_int64, ct.POINTER(ct.c_int32), P, ct.c_size_t]),
+            "psl_release": (ct.c_int, [P, ct.c_int64]),
+            "psl_export_state": (ct.c_int, [P, ct.c_int64, ct.POINTER(psl_walk_state), P, P, P, P, ct.c_size_t]),
+            "psl_trace": (ct.c_int, [P, ct.c_int64, P, ct.c_size_t]),
+            "psl_autocorr": (ct.c_int, [P, P, ct.c_uint32, ct.c_uint32, P]),
+            "psl_walk_bytes": (ct.c_uint64, [ct.c_uint32, ct.c_int32, ct.c_uint32]),
+            "psl_shutdown": (None, [P]),
+            "psl_last_error": (ct.c_char_p, [P]),
+            "psl_profile": (ct.c_int, [P, ct.c_int]),
+            "psl_profile_read": (ct.c_int, [P, ct.POINTER(psl_kernel_time), ct.c_size_t]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray | None):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data
+
+
+def limbs_to_int(limbs) -> int:
+    v = 0
+    for i, w in enumerate(limbs):
+        v |= int(w) << (32 * i)
+    if v >> (32 * WIDE - 1):
+        v -= 1 << (32 * WIDE)
+    return v
+
+
+# ---- C-ABI mirrors ---------------------------------------------------------------------------
+def psl_config_default() -> psl_config:
+    c = psl_config()
+    lib().psl_config_default(ct.byref(c))
+    return c
+
+
+def psl_last_error(ctx) -> str:
+    r = lib().psl_last_error(ctx)
+    return r.decode() if r else ""
+
+
+def _check(ctx, rc: int) -> int:
+    if rc < 0:
+        raise PslError(rc, psl_last_error(ctx))
+    return rc
+
+
+def psl_init(cfg: psl_config):
+    h = ct.c_void_p()
+    _check(None, lib().psl_init(ct.byref(cfg), ct.byref(h)))
+    return h
+
+
+def psl_submit(ctx, L, seed, alpha1, alpha2, budget) -> int:
+    return _check(ctx, lib().psl_submit(ctx, L, seed, float(alpha1), float(alpha2), budget))
+
+
+def psl_submit_ex(ctx, p: psl_walk_params) -> int:
+    return _check(ctx, lib().psl_submit_ex(ctx, ct.byref(p)))
+
+
+def psl_step(ctx, max_moves: int) -> int:
+    return _check(ctx, lib().psl_step(ctx, max_moves))
+
+
+def psl_poll(ctx, wid: int) -> dict:
+    st = psl_status()
+    _check(ctx, lib().psl_poll(ctx, wid, ct.byref(st)))
+    return {f: getattr(st, f) for f, _ in psl_status._fields_ if f != "pad"}
+
+
+def psl_best(ctx, wid: int, L: int):
+    seq = np.zeros(L, dtype=np.int8)
+    p = ct.c_int32()
+    _check(ctx, lib().psl_best(ctx, wid, ct.byref(p), _ptr(seq), L))
+    return int(p.value), seq
+
+
+def psl_release(ctx, wid: int) -> None:
+    _check(ctx, lib().psl_release(ctx, wid))
+
+
+def psl_export_state(ctx, wid: int, L: int) -> dict:
+    st = psl_walk_state()
+    piv, lb, sb = (np.zeros(L, dtype=np.int8) for _ in range(3))
+    C = np.zeros(L, dtype=np.int32)
+    _check(ctx, lib().psl_export_state(ctx, wid, ct.byref(st), _ptr(piv), _ptr(lb), _ptr(sb), _ptr(C), L))
+    d = {f: getattr(st, f) for f, _ in psl_walk_state._fields_ if f not in ("pad", "F", "value_local")}
+    d["F"] = limbs_to_int(st.F)
+    d["value_local"] = limbs_to_int(st.value_local)
+    d.update(pivot=piv, local_best=lb, sol_best=sb, C=C)
+    return d
+
+
+def psl_trace(ctx, wid: int, cap: int) -> np.ndarray:
+    out = np.zeros(cap, dtype=TRACE_DTYPE)
+    n = _check(ctx, lib().psl_trace(ctx, wid, _ptr(out) if cap else None, cap))
+    return out[:n]
+
+
+def psl_autocorr(ctx, seqs: np.ndarray) -> np.ndarray:
+    seqs = np.ascontiguousarray(np.atleast_2d(seqs), dtype=np.int8)
+    n, L = seqs.shape
+    C = np.zeros((n, L), dtype=np.int32)
+    _check(ctx, lib().psl_autocorr(ctx, _ptr(seqs), n, L, _ptr(C)))
+    return C
+
+
+def psl_walk_bytes(L: int, n_lmt: int = 6912, trace_cap: int = 0) -> int:
+    return int(lib().psl_walk_bytes(L, n_lmt, trace_cap))
+
+
+def psl_shutdown(ctx) -> None:
+    lib().psl_shutdown(ctx)
+
+
+def psl_profile(ctx, enable: bool) -> None:
+    _check(ctx, lib().psl_profile(ctx, 1 if enable else 0))
+
+
+def psl_profile_read(ctx) -> dict:
+    arr = (psl_kernel_time * 16)()
+    n = _check(ctx, lib().psl_profile_read(ctx, arr, 16))
+    return {arr[k].name.decode(): (int(arr[k].launches), float(arr[k].total_ms)) for k in range(n)}
+
+
+# ---- convenience wrapper ---------------------------------------------------------------------
+class Context:
+    """One library context.  Device memory may come from a torch tensor (``arena_tensor``)
+    and work may be issued on a torch stream (``stream``); torch is plumbing only."""
+
+    def __init__(self, *, form: str = "batched", arena_bytes: int = 0, arena_tensor=None, stream=None,
+                 max_walks: int = 4096, n_lmt: int = 6912, ls_lmt: int = 2000, flip_lmt: int = 10, device: int = 0,
+                 hot_tile_sb: int = 0, steps_per_graph: int = 0):
+        cfg = psl_config_default()
+        cfg.n_lmt, cfg.ls_lmt, cfg.flip_lmt, cfg.device = n_lmt, ls_lmt, flip_lmt, device
+        cfg.form = PSL_FORM_PLAIN if form == "plain" else PSL_FORM_BATCHED
+        cfg.max_walks, cfg.hot_tile_sb, cfg.steps_per_graph = max_walks, hot_tile_sb, steps_per_graph
+        self._arena_tensor = arena_tensor
+        if arena_tensor is not None:
+            cfg.arena = arena_tensor.data_ptr()
+            cfg.arena_bytes = arena_tensor.numel() * arena_tensor.element_size()
+        else:
+            cfg.arena_bytes = arena_bytes
+        if stream is not None:
+            cfg.stream = stream if isinstance(stream, int) else stream.cuda_stream
+        self.h = psl_init(cfg)
+        self.L_of: dict[int, int] = {}
+
+    def submit(self, L, seed, alpha1, alpha2, budget) -> int:
+        wid = psl_submit(self.h, L, seed, alpha1, alpha2, budget)
+        self.L_of[wid] = L
+        return wid
+
+    def submit_ex(self, L, seed, alpha1=4, alpha2=13, budget=2000, *, n_lmt=0, ls_lmt=-1, flip_lmt=0, topk=1,
+                  init_seq=None, trace_cap=0) -> int:
+        seq = None if init_seq is None else np.ascontiguousarray(init_seq, dtype=np.int8)
+        p = psl_walk_params(L, seed, alpha1, alpha2, budget, n_lmt, ls_lmt, flip_lmt, topk,
+                            None if seq is None else seq.ctypes.data, trace_cap)
+        wid = psl_submit_ex(self.h, p)
+        self.L_of[wid] = L
+        return wid
+
+    def step(self, max_moves: int) -> int:
+        return psl_step(self.h, max_moves)
+
+    def run(self, chunk: int = 1 << 30) -> None:
+        while self.step(chunk) > 0:
+            pass
+
+    def poll(self, wid: int) -> dict:
+        return psl_poll(self.h, wid)
+
+    def best(self, wid: int):
+        return psl_best(self.h, wid, self.L_of[wid])
+
+    def release(self, wid: int) -> None:
+        psl_release(self.h, wid)
+        self.L_of.pop(wid, None)
+
+    def export_state(self, wid: int) -> dict:
+        return psl_export_state(self.h, wid, self.L_of[wid])
+
+    def trace(self, wid: int, cap: int) -> np.ndarray:
+        return psl_trace(self.h, wid, cap)
+
+    def autocorr(self, seqs) -> np.ndarray:
+        return psl_autocorr(self.h, seqs)
+
+    def profile(self, enable: bool = True) -> None:
+        psl_profile(self.h, enable)
+
+    def profile_read(self) -> dict:
+        return psl_profile_read(self.h)
+
+    def close(self) -> None:
+        if self.h:
+            psl_shutdown(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

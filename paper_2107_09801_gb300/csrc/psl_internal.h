@@ -1,0 +1,122 @@
+// psl_internal.h -- device-resident walk state and launch interface shared by the
+// kernels (psl_kernels.cu) and the host runtime (psl_runtime.cu).  GPU side only.
+//
+// Notation (0-based, as in the library header): s_0..s_{L-1} in {+1,-1}, packed
+// one bit per element, bit = 1 meaning s = -1.  C_k (Eq. 2), PSL (Eq. 3),
+// F = sum_{k>=1} |C_k|^alpha (Eq. 4).  A "window" is the limited neighbourhood of
+// Algorithm 1: N = min(N_lmt, L) neighbours j = (start + i) % L, i = 1..N.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace psl {
+
+constexpr int kGuardWords = 2;     // zero words before and after every packed sequence
+constexpr int kWideLimbs = 12;     // exact fitness: 384-bit, 12 x 32-bit limbs
+constexpr int kMaxFlips = 64;      // upper bound on FLIP_lmt actually applied
+constexpr int kQcap = 64;          // exact re-check candidates handled per pass of the grid
+constexpr int kApplyChunk = 8192;  // k per CTA in the O(L) update pass
+constexpr int kRecheckChunk = 16384;  // k per CTA in the exact re-check
+constexpr int kSbK = 30;           // k per super-block (6 groups of 5)
+constexpr int kGroupK = 5;         // k per table group (32-entry tables)
+constexpr int kApplyPartStride = 32;  // u32 per apply-chunk partial record
+constexpr int kFlushBlockAdds = 64;   // FP32 additions per lane before a compensated flush
+
+enum WalkStatus : uint32_t { kFree = 0, kRunning = 1, kDone = 2, kError = 3 };
+enum ApplyMode : uint32_t { kModeInit = 0, kModeMove = 1, kModeSwitch = 2 };
+enum TraceFlags : uint32_t { kImproved = 1, kWorse = 2, kSwitch = 4, kPslBest = 8 };
+
+// Per-step record kept on the device when a walk asks for a trace.
+struct TraceRec {
+  uint64_t step;
+  uint32_t start, kstar, alpha, unimproved;
+  int32_t psl, psl_best, win_psl;
+  uint32_t win_psl_j, flags, nflip, ncand;
+  float score_kstar, score_min, bound;
+  uint32_t pad;
+  double value_step;              // exact F of the chosen neighbour, rounded to FP64
+  uint32_t value_exact[kWideLimbs];
+};
+
+// One walk slot.  Static fields are written by the host at admission; dynamic
+// fields are owned by the device while the walk runs.
+struct WalkDev {
+  // ---- static ----
+  uint32_t L, N, nw, nflip;
+  uint32_t alpha1, alpha2, ls_lmt, topk;
+  uint64_t seed, budget;
+  uint32_t nchunk_apply, nchunk_rc, trace_cap, has_init_seq;
+  uint32_t *bits, *bits_local, *bits_best;  // logical word 0 (guards before and after)
+  int32_t *C, *C_local;
+  float4 *T;          // per k: (Tp4, Tm4, Tp2, Tm2), scaled by 2^(-alpha*e)
+  float *score;       // FP32 filter score of window position i at [i-1]
+  int32_t *pslj;      // exact neighbour PSL (or INT32_MAX when not needed)
+  int2 *ktau;         // near-peak list (k, C_k)
+  uint32_t *cand;     // candidate window positions, ascending
+  uint32_t *rc_part;  // exact re-check partials [cand][chunk][2*kWideLimbs]
+  uint32_t *ap_part;  // update-pass partials [chunk][kApplyPartStride]
+  TraceRec *trace;
+  // ---- dynamic ----
+  uint32_t status, error;
+  uint32_t alpha, unimproved;
+  int32_t psl, psl_best, psl_local;
+  uint32_t start;
+  uint64_t rng_ctr, moves, flip_evals, switches, rechecks;
+  int32_t e;              // table scale exponent: 2^e >= max|C| + 4 over the next window
+  float S_abs;            // sum_k max |T_k| (bounds the FP32 error of every score)
+  uint32_t nktau, ktau_on;
+  int32_t ktau_thr;       // list threshold on |C_k| for the running update pass
+  uint32_t ncand;
+  uint32_t kstar, kstar_i;
+  uint32_t mode, improved, psl_improved, psl_j;
+  int32_t win_psl;
+  uint32_t win_psl_i;
+  uint32_t arrive;
+  uint32_t alpha_next;
+  float score_min, bound;
+  uint32_t flips[kMaxFlips];
+  uint32_t F[kWideLimbs], value_local[kWideLimbs], value_step[kWideLimbs];
+};
+
+// One unit of the neighbourhood kernel: a block of consecutive window positions.
+struct HotItem {
+  uint32_t slot;
+  uint32_t i0;  // first window position (1-based) of the block
+};
+
+struct LaunchCtx {
+  WalkDev *hdr;          // device array of walk slots
+  const uint32_t *active;  // device list of active slots
+  uint32_t nactive;
+  const HotItem *items;  // device list of neighbourhood blocks
+  uint32_t nitems;
+  uint32_t max_chunk_apply, max_chunk_rc;
+  uint32_t hot_threads;  // neighbours per block of the batched kernel
+  uint32_t hot_tile_sb;  // super-blocks per k-tile
+  cudaStream_t stream;
+};
+
+// ---- launchers (psl_kernels.cu) ----
+cudaError_t prepare_kernels();  // one-off kernel attributes (call before any capture)
+cudaError_t launch_init_bits(const LaunchCtx &c);
+cudaError_t launch_autocorr(const LaunchCtx &c, uint32_t maxL);
+cudaError_t launch_apply(const LaunchCtx &c);
+cudaError_t launch_hot_batched(const LaunchCtx &c);
+cudaError_t launch_hot_plain(WalkDev *hdr_one, uint32_t N, cudaStream_t s);
+cudaError_t launch_select(const LaunchCtx &c);
+cudaError_t launch_recheck(const LaunchCtx &c);
+cudaError_t launch_decide(const LaunchCtx &c);
+cudaError_t launch_start_init(const LaunchCtx &c);
+size_t hot_batched_smem(uint32_t tile_sb);
+
+// Candidate threshold shared bit-for-bit by the device select and the host select
+// of the plain form.  Returns the largest FP32 score that may still belong to the
+// exact argmin: min + 2B rounded up, with B bounding |FP32 score - exact score|.
+__host__ __device__ inline double score_bound(float S_abs, uint32_t alpha, uint32_t L) {
+  const double u = 5.9604644775390625e-08;  // 2^-24
+  const double nflush = (double)(L / kSbK + 2);
+  const double rel = (2.0 * alpha + 68.0) * u + (nflush * u) * (nflush * u);
+  return rel * (double)S_abs * 1.01 + (double)L * 7.52316384526264e-37;  // + L * 2^-120
+}
+
+}  // namespace psl

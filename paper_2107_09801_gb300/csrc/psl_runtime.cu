@@ -1,0 +1,959 @@
+// psl_runtime.cu -- host runtime behind the C ABI of include/psl.h: device arena,
+// walk slots, admission of queued walks by device memory, the batched and plain
+// step loops (Algorithm 1 of arXiv 2107.09801) and state export.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "psl.h"
+#include "psl_internal.h"
+
+using namespace psl;
+
+namespace {
+
+thread_local std::string g_init_error;
+
+enum ProfKind { kPHot = 0, kPSelect, kPRecheck, kPDecide, kPApply, kPHotPlain, kPInit, kPGraph, kProfKinds };
+const char *kProfNames[kProfKinds] = {"hot", "select", "recheck", "decide", "apply", "hot_plain", "init", "graph"};
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Layout {
+  size_t bits, bits_local, bits_best, C, C_local, T, score, pslj, ktau, cand, rc_part, ap_part, trace, total;
+};
+
+Layout layout_for(uint32_t L, uint32_t N, uint32_t trace_cap) {
+  Layout o{};
+  const size_t nw = (L + 31) / 32;
+  const size_t words = nw + 2 * kGuardWords;
+  const size_t nchunk_rc = (L + kRecheckChunk - 1) / kRecheckChunk;
+  const size_t nchunk_ap = (L + kApplyChunk - 1) / kApplyChunk;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes, 256);
+    return at;
+  };
+  o.bits = take(words * 4);
+  o.bits_local = take(words * 4);
+  o.bits_best = take(words * 4);
+  o.C = take((size_t)L * 4);
+  o.C_local = take((size_t)L * 4);
+  o.T = take((size_t)L * 16);
+  o.score = take((size_t)N * 4);
+  o.pslj = take((size_t)N * 4);
+  o.ktau = take((size_t)L * 8);
+  o.cand = take((size_t)N * 4);
+  o.rc_part = take(((size_t)kQcap * nchunk_rc + N) * kWideLimbs * 4);
+  o.ap_part = take(nchunk_ap * kApplyPartStride * 4);
+  o.trace = take((size_t)trace_cap * sizeof(TraceRec));
+  o.total = off;
+  return o;
+}
+
+// First-fit allocator over the arena with coalescing free list.
+struct Arena {
+  size_t size = 0;
+  std::map<size_t, size_t> free_;  // offset -> length
+  void reset(size_t n) {
+    size = n;
+    free_.clear();
+    if (n) free_[0] = n;
+  }
+  bool alloc(size_t n, size_t *off) {
+    n = align_up(n, 256);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second >= n) {
+        *off = it->first;
+        const size_t rest = it->second - n, at = it->first + n;
+        free_.erase(it);
+        if (rest) free_[at] = rest;
+        return true;
+      }
+    }
+    return false;
+  }
+  void release(size_t off, size_t n) {
+    n = align_up(n, 256);
+    auto it = free_.emplace(off, n).first;
+    auto nx = std::next(it);
+    if (nx != free_.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_.erase(nx);
+    }
+    if (it != free_.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_.erase(it);
+      }
+    }
+  }
+};
+
+struct HostWalk {
+  int64_t id = -1;
+  psl_walk_params p{};
+  std::vector<int8_t> init_seq;
+  int32_t state = PSL_QUEUED;
+  int32_t error = 0;
+  int32_t slot = -1;
+  size_t off = 0, bytes = 0;
+  Layout lay{};
+  double t_submit = 0, t_start = 0, t_done = 0;
+};
+
+}  // namespace
+
+struct psl_ctx {
+  psl_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  char *arena = nullptr;
+  bool own_arena = false;
+  Arena alloc;
+  WalkDev *d_hdr = nullptr;
+  std::vector<WalkDev> h_hdr;
+  uint32_t *d_active = nullptr;
+  HotItem *d_items = nullptr;
+  uint32_t items_cap = 0;
+  uint32_t *h_pinned = nullptr;
+  std::vector<int32_t> free_slots;
+  std::map<int64_t, HostWalk> walks;
+  std::deque<int64_t> queue;
+  std::vector<uint32_t> active;  // running slots
+  bool active_dirty = true;
+  uint32_t nitems = 0, max_chunk_apply = 1, max_chunk_rc = 1;
+  int64_t next_id = 0;
+  std::string err;
+  // CUDA graph of steps_per_graph steps over the current active set
+  cudaGraphExec_t graph = nullptr;
+  uint32_t graph_steps = 0;
+  // CUDA-event profile of kernel launches
+  bool prof = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+  std::vector<int> ev_kind;
+  size_t ev_used = 0;
+  double prof_ms[kProfKinds] = {};
+  uint64_t prof_n[kProfKinds] = {};
+};
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e__ = (call);                                                             \
+    if (e__ != cudaSuccess) return fail(ctx, PSL_ECUDA, "%s: %s", #call, cudaGetErrorString(e__)); \
+  } while (0)
+
+static int fail(psl_ctx *ctx, int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (ctx)
+    ctx->err = buf;
+  else
+    g_init_error = buf;
+  return code;
+}
+
+// Records an event pair around one launch when profiling is on.
+static cudaError_t prof_begin(psl_ctx *ctx, int kind) {
+  if (!ctx->prof) return cudaSuccess;
+  if (ctx->ev_used == ctx->ev.size()) {
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e != cudaSuccess) return e;
+    ctx->ev.push_back({a, b});
+    ctx->ev_kind.push_back(kind);
+  }
+  ctx->ev_kind[ctx->ev_used] = kind;
+  return cudaEventRecord(ctx->ev[ctx->ev_used].first, ctx->stream);
+}
+
+static cudaError_t prof_end(psl_ctx *ctx) {
+  if (!ctx->prof) return cudaSuccess;
+  return cudaEventRecord(ctx->ev[ctx->ev_used++].second, ctx->stream);
+}
+
+// Folds the recorded pairs into the totals (the stream must be synchronised).
+static void prof_collect(psl_ctx *ctx) {
+  for (size_t i = 0; i < ctx->ev_used; i++) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->ev[i].first, ctx->ev[i].second) == cudaSuccess) {
+      ctx->prof_ms[ctx->ev_kind[i]] += ms;
+      ctx->prof_n[ctx->ev_kind[i]] += 1;
+    }
+  }
+  ctx->ev_used = 0;
+}
+
+extern "C" int psl_profile(psl_ctx *ctx, int enable) {
+  if (!ctx) return PSL_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_collect(ctx);
+  ctx->prof = enable != 0;
+  if (ctx->prof)
+    for (int k = 0; k < kProfKinds; k++) ctx->prof_ms[k] = 0.0, ctx->prof_n[k] = 0;
+  return PSL_OK;
+}
+
+extern "C" int psl_profile_read(psl_ctx *ctx, psl_kernel_time *out, size_t cap) {
+  if (!ctx || (!out && cap)) return PSL_EINVAL;
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_collect(ctx);
+  for (size_t k = 0; k < cap && k < (size_t)kProfKinds; k++) {
+    std::memset(&out[k], 0, sizeof out[k]);
+    std::snprintf(out[k].name, sizeof out[k].name, "%s", kProfNames[k]);
+    out[k].launches = ctx->prof_n[k];
+    out[k].total_ms = ctx->prof_ms[k];
+  }
+  return kProfKinds;
+}
+
+extern "C" void psl_config_default(psl_config *cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->n_lmt = 6912;
+  cfg->ls_lmt = 2000;
+  cfg->flip_lmt = 10;
+  cfg->device = 0;
+  cfg->form = PSL_FORM_BATCHED;
+  cfg->max_walks = 4096;
+  cfg->hot_tile_sb = 0;
+  cfg->steps_per_graph = 0;
+}
+
+extern "C" uint64_t psl_walk_bytes(uint32_t L, int32_t n_lmt, uint32_t trace_cap) {
+  if (L < 2) return 0;
+  const uint32_t N = (n_lmt <= 0) ? L : std::min<uint32_t>((uint32_t)n_lmt, L);
+  return layout_for(L, N, trace_cap).total;
+}
+
+extern "C" const char *psl_last_error(psl_ctx *ctx) { return ctx ? ctx->err.c_str() : g_init_error.c_str(); }
+
+extern "C" int psl_init(const psl_config *cfg_in, psl_ctx **out) {
+  if (!out) return fail(nullptr, PSL_EINVAL, "out is NULL");
+  *out = nullptr;
+  psl_config cfg;
+  if (cfg_in)
+    cfg = *cfg_in;
+  else
+    psl_config_default(&cfg);
+  if (cfg.n_lmt < 1 || cfg.ls_lmt < 0 || cfg.flip_lmt < 0 || cfg.flip_lmt > kMaxFlips || cfg.max_walks < 1 ||
+      (cfg.form != PSL_FORM_BATCHED && cfg.form != PSL_FORM_PLAIN) || cfg.hot_tile_sb < 0 || cfg.hot_tile_sb > 80 ||
+      cfg.steps_per_graph < 0)
+    return fail(nullptr, PSL_EINVAL, "invalid psl_config field");
+  if (cfg.arena && cfg.arena_bytes == 0) return fail(nullptr, PSL_EINVAL, "arena given without arena_bytes");
+  psl_ctx *ctx = new psl_ctx();
+  ctx->cfg = cfg;
+  if (ctx->cfg.hot_tile_sb == 0) ctx->cfg.hot_tile_sb = 32;
+  auto bail = [&](int code) {
+    psl_shutdown(ctx);
+    return code;
+  };
+  cudaError_t e = cudaSetDevice(cfg.device);
+  if (e != cudaSuccess) {
+    fail(nullptr, PSL_ECUDA, "cudaSetDevice(%d): %s", cfg.device, cudaGetErrorString(e));
+    delete ctx;
+    return PSL_ECUDA;
+  }
+  if (cfg.stream) {
+    ctx->stream = (cudaStream_t)cfg.stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      fail(nullptr, PSL_ECUDA, "cudaStreamCreate failed");
+      delete ctx;
+      return PSL_ECUDA;
+    }
+    ctx->own_stream = true;
+  }
+  size_t bytes = cfg.arena_bytes;
+  if (cfg.arena) {
+    ctx->arena = (char *)cfg.arena;
+  } else {
+    if (bytes == 0) {
+      size_t fr = 0, tot = 0;
+      if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+        fail(nullptr, PSL_ECUDA, "cudaMemGetInfo failed");
+        return bail(PSL_ECUDA);
+      }
+      bytes = std::min<size_t>(fr / 2, (size_t)64 << 30);
+    }
+    if (cudaMalloc(&ctx->arena, bytes) != cudaSuccess) {
+      cudaGetLastError();
+      fail(nullptr, PSL_ENOMEM, "cudaMalloc(arena %zu bytes) failed", bytes);
+      return bail(PSL_ENOMEM);
+    }
+    ctx->own_arena = true;
+  }
+  if (prepare_kernels() != cudaSuccess) {
+    cudaGetLastError();
+    fail(nullptr, PSL_ECUDA, "kernel attribute setup failed");
+    return bail(PSL_ECUDA);
+  }
+  ctx->alloc.reset(bytes);
+  ctx->h_hdr.assign(cfg.max_walks, WalkDev{});
+  if (cudaMalloc(&ctx->d_hdr, sizeof(WalkDev) * cfg.max_walks) != cudaSuccess ||
+      cudaMalloc(&ctx->d_active, sizeof(uint32_t) * cfg.max_walks) != cudaSuccess ||
+      cudaMallocHost(&ctx->h_pinned, sizeof(uint32_t) * cfg.max_walks) != cudaSuccess) {
+    cudaGetLastError();
+    fail(nullptr, PSL_ENOMEM, "slot table allocation failed");
+    return bail(PSL_ENOMEM);
+  }
+  cudaMemset(ctx->d_hdr, 0, sizeof(WalkDev) * cfg.max_walks);
+  for (int s = cfg.max_walks - 1; s >= 0; s--) ctx->free_slots.push_back(s);
+  *out = ctx;
+  return PSL_OK;
+}
+
+extern "C" void psl_shutdown(psl_ctx *ctx) {
+  if (!ctx) return;
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  for (auto &pr : ctx->ev) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  if (ctx->own_arena && ctx->arena) cudaFree(ctx->arena);
+  if (ctx->d_hdr) cudaFree(ctx->d_hdr);
+  if (ctx->d_active) cudaFree(ctx->d_active);
+  if (ctx->d_items) cudaFree(ctx->d_items);
+  if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
+  if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+  delete ctx;
+}
+
+static int check_params(psl_ctx *ctx, psl_walk_params &p) {
+  if (p.L < 2 || p.L > (1u << 20) - 1u) return fail(ctx, PSL_EINVAL, "L=%u outside 2..2^20-1", p.L);
+  if (p.alpha1 < 1 || p.alpha1 > 16 || p.alpha2 < 1 || p.alpha2 > 16)
+    return fail(ctx, PSL_EINVAL, "alpha must be an integer in 1..16");
+  if (p.budget < 1) return fail(ctx, PSL_EINVAL, "budget must be >= 1");
+  if (p.n_lmt <= 0) p.n_lmt = ctx->cfg.n_lmt;
+  if (p.ls_lmt < 0) p.ls_lmt = ctx->cfg.ls_lmt;  // 0 is a valid LS_lmt
+  if (p.flip_lmt <= 0) p.flip_lmt = ctx->cfg.flip_lmt;
+  if (p.flip_lmt > kMaxFlips) return fail(ctx, PSL_EINVAL, "flip_lmt > %d", kMaxFlips);
+  if (p.topk <= 0) p.topk = 1;
+  if (p.topk > 16) return fail(ctx, PSL_EINVAL, "topk > 16");
+  return PSL_OK;
+}
+
+extern "C" int64_t psl_submit_ex(psl_ctx *ctx, const psl_walk_params *pin) {
+  if (!ctx || !pin) return PSL_EINVAL;
+  psl_walk_params p = *pin;
+  int rc = check_params(ctx, p);
+  if (rc) return rc;
+  HostWalk w;
+  w.id = ctx->next_id++;
+  w.p = p;
+  if (p.init_seq) {
+    w.init_seq.assign(p.init_seq, p.init_seq + p.L);
+    for (int8_t v : w.init_seq)
+      if (v != 1 && v != -1) return fail(ctx, PSL_EINVAL, "init_seq values must be +1 or -1");
+  }
+  w.p.init_seq = nullptr;
+  const uint32_t N = std::min<uint32_t>((uint32_t)p.n_lmt, p.L);
+  w.lay = layout_for(p.L, N, p.trace_cap);
+  w.bytes = w.lay.total;
+  if (w.bytes > ctx->alloc.size) return fail(ctx, PSL_ENOMEM, "walk needs %zu bytes, arena holds %zu", w.bytes,
+                                             ctx->alloc.size);
+  w.t_submit = now_s();
+  const int64_t id = w.id;
+  ctx->walks.emplace(id, std::move(w));
+  ctx->queue.push_back(id);
+  return id;
+}
+
+extern "C" int64_t psl_submit(psl_ctx *ctx, uint32_t L, uint64_t seed, double alpha1, double alpha2,
+                              uint64_t budget) {
+  if (!ctx) return PSL_EINVAL;
+  if (alpha1 != std::floor(alpha1) || alpha2 != std::floor(alpha2))
+    return fail(ctx, PSL_EINVAL, "alpha must be an integer");
+  psl_walk_params p{};
+  p.L = L;
+  p.seed = seed;
+  p.alpha1 = (int32_t)std::max(-1.0, std::min(alpha1, 1e6));
+  p.alpha2 = (int32_t)std::max(-1.0, std::min(alpha2, 1e6));
+  p.budget = budget;
+  p.ls_lmt = -1;
+  return psl_submit_ex(ctx, &p);
+}
+
+// ---------------------------------------------------------------------------------
+// admission and launch plumbing
+// ---------------------------------------------------------------------------------
+static void fill_header(psl_ctx *ctx, HostWalk &w, WalkDev &h) {
+  std::memset(&h, 0, sizeof h);
+  const psl_walk_params &p = w.p;
+  char *base = ctx->arena + w.off;
+  h.L = p.L;
+  h.N = std::min<uint32_t>((uint32_t)p.n_lmt, p.L);
+  h.nw = (p.L + 31) / 32;
+  h.nflip = std::min<uint32_t>((uint32_t)p.flip_lmt, p.L);
+  h.alpha1 = (uint32_t)p.alpha1;
+  h.alpha2 = (uint32_t)p.alpha2;
+  h.ls_lmt = (uint32_t)p.ls_lmt;
+  h.topk = (uint32_t)p.topk;
+  h.seed = p.seed;
+  h.budget = p.budget;
+  h.nchunk_apply = (p.L + kApplyChunk - 1) / kApplyChunk;
+  h.nchunk_rc = (p.L + kRecheckChunk - 1) / kRecheckChunk;
+  h.trace_cap = p.trace_cap;
+  h.has_init_seq = w.init_seq.empty() ? 0u : 1u;
+  h.bits = (uint32_t *)(base + w.lay.bits) + kGuardWords;
+  h.bits_local = (uint32_t *)(base + w.lay.bits_local) + kGuardWords;
+  h.bits_best = (uint32_t *)(base + w.lay.bits_best) + kGuardWords;
+  h.C = (int32_t *)(base + w.lay.C);
+  h.C_local = (int32_t *)(base + w.lay.C_local);
+  h.T = (float4 *)(base + w.lay.T);
+  h.score = (float *)(base + w.lay.score);
+  h.pslj = (int32_t *)(base + w.lay.pslj);
+  h.ktau = (int2 *)(base + w.lay.ktau);
+  h.cand = (uint32_t *)(base + w.lay.cand);
+  h.rc_part = (uint32_t *)(base + w.lay.rc_part);
+  h.ap_part = (uint32_t *)(base + w.lay.ap_part);
+  h.trace = p.trace_cap ? (TraceRec *)(base + w.lay.trace) : nullptr;
+  h.status = kRunning;
+  h.alpha = h.alpha1;
+  h.alpha_next = h.alpha1;
+  h.rng_ctr = (p.L + 63) / 64;
+}
+
+static int rebuild_active(psl_ctx *ctx) {
+  ctx->active.clear();
+  for (auto &kv : ctx->walks)
+    if (kv.second.state == PSL_RUNNING) ctx->active.push_back((uint32_t)kv.second.slot);
+  // long walks first: their blocks are the longest-running units
+  std::sort(ctx->active.begin(), ctx->active.end(),
+            [&](uint32_t a, uint32_t b) { return ctx->h_hdr[a].L > ctx->h_hdr[b].L; });
+  std::vector<HotItem> items;
+  ctx->max_chunk_apply = 1;
+  ctx->max_chunk_rc = 1;
+  for (uint32_t s : ctx->active) {
+    const WalkDev &h = ctx->h_hdr[s];
+    for (uint32_t i0 = 1; i0 <= h.N; i0 += 256) items.push_back(HotItem{s, i0});
+    ctx->max_chunk_apply = std::max(ctx->max_chunk_apply, h.nchunk_apply);
+    ctx->max_chunk_rc = std::max(ctx->max_chunk_rc, h.nchunk_rc);
+  }
+  if (items.size() > ctx->items_cap) {
+    if (ctx->d_items) cudaFree(ctx->d_items);
+    ctx->items_cap = (uint32_t)std::max<size_t>(items.size(), 1024);
+    CK(cudaMalloc(&ctx->d_items, sizeof(HotItem) * ctx->items_cap));
+  }
+  ctx->nitems = (uint32_t)items.size();
+  if (!items.empty())
+    CK(cudaMemcpyAsync(ctx->d_items, items.data(), sizeof(HotItem) * items.size(), cudaMemcpyHostToDevice,
+                       ctx->stream));
+  if (!ctx->active.empty()) {
+    std::copy(ctx->active.begin(), ctx->active.end(), ctx->h_pinned);
+    CK(cudaMemcpyAsync(ctx->d_active, ctx->h_pinned, sizeof(uint32_t) * ctx->active.size(),
+                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));  // h_pinned is reused
+  }
+  if (ctx->graph) {
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  ctx->active_dirty = false;
+  return PSL_OK;
+}
+
+static LaunchCtx launch_ctx(psl_ctx *ctx, const uint32_t *d_list, uint32_t n) {
+  LaunchCtx c{};
+  c.hdr = ctx->d_hdr;
+  c.active = d_list;
+  c.nactive = n;
+  c.items = ctx->d_items;
+  c.nitems = ctx->nitems;
+  c.max_chunk_apply = ctx->max_chunk_apply;
+  c.max_chunk_rc = ctx->max_chunk_rc;
+  c.hot_threads = 256;
+  c.hot_tile_sb = (uint32_t)ctx->cfg.hot_tile_sb;
+  c.stream = ctx->stream;
+  return c;
+}
+
+static void pack_pm1(const int8_t *s, uint32_t L, std::vector<uint32_t> &words) {
+  words.assign((L + 31) / 32, 0u);
+  for (uint32_t i = 0; i < L; i++)
+    if (s[i] < 0) words[i >> 5] |= 1u << (i & 31);
+}
+
+// Admits queued walks (FIFO, skipping those that do not fit yet) and initialises them.
+static int admit(psl_ctx *ctx) {
+  std::vector<uint32_t> fresh;
+  uint32_t maxL = 0, maxchunk = 1;
+  for (auto it = ctx->queue.begin(); it != ctx->queue.end();) {
+    HostWalk &w = ctx->walks.at(*it);
+    if (ctx->free_slots.empty()) break;
+    size_t off;
+    if (!ctx->alloc.alloc(w.bytes, &off)) {
+      ++it;
+      continue;
+    }
+    w.off = off;
+    w.slot = ctx->free_slots.back();
+    ctx->free_slots.pop_back();
+    w.state = PSL_RUNNING;
+    w.t_start = now_s();
+    WalkDev &h = ctx->h_hdr[w.slot];
+    fill_header(ctx, w, h);
+    CK(cudaMemcpyAsync(ctx->d_hdr + w.slot, &h, sizeof(WalkDev), cudaMemcpyHostToDevice, ctx->stream));
+    if (!w.init_seq.empty()) {
+      std::vector<uint32_t> words;
+      pack_pm1(w.init_seq.data(), w.p.L, words);
+      CK(cudaMemcpyAsync(h.bits, words.data(), words.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));  // words is a temporary
+    }
+    fresh.push_back((uint32_t)w.slot);
+    maxL = std::max(maxL, w.p.L);
+    maxchunk = std::max(maxchunk, h.nchunk_apply);
+    it = ctx->queue.erase(it);
+  }
+  if (fresh.empty()) return PSL_OK;
+  uint32_t *d_fresh = nullptr;
+  CK(cudaMalloc(&d_fresh, sizeof(uint32_t) * fresh.size()));
+  CK(cudaMemcpyAsync(d_fresh, fresh.data(), sizeof(uint32_t) * fresh.size(), cudaMemcpyHostToDevice, ctx->stream));
+  LaunchCtx c = launch_ctx(ctx, d_fresh, (uint32_t)fresh.size());
+  c.max_chunk_apply = maxchunk;
+  cudaError_t e = prof_begin(ctx, kPInit);
+  if (e == cudaSuccess) e = launch_init_bits(c);
+  if (e == cudaSuccess) e = launch_autocorr(c, maxL);
+  if (e == cudaSuccess) e = launch_start_init(c);
+  if (e == cudaSuccess) e = launch_apply(c);
+  if (e == cudaSuccess) e = prof_end(ctx);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  if (e == cudaSuccess) prof_collect(ctx);
+  cudaFree(d_fresh);
+  if (e != cudaSuccess) return fail(ctx, PSL_ECUDA, "walk initialisation: %s", cudaGetErrorString(e));
+  ctx->active_dirty = true;
+  return PSL_OK;
+}
+
+static int refresh_headers(psl_ctx *ctx) {
+  // copy back the slot headers (one contiguous copy up to the highest running slot)
+  uint32_t top = 0;
+  for (uint32_t s : ctx->active) top = std::max(top, s + 1);
+  std::vector<WalkDev> tmp(top);
+  if (top) {
+    CK(cudaMemcpyAsync(tmp.data(), ctx->d_hdr, sizeof(WalkDev) * top, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    for (uint32_t s : ctx->active) ctx->h_hdr[s] = tmp[s];
+  }
+  prof_collect(ctx);
+  const double t = now_s();
+  for (auto &kv : ctx->walks) {
+    HostWalk &w = kv.second;
+    if (w.state != PSL_RUNNING) continue;
+    const WalkDev &h = ctx->h_hdr[w.slot];
+    if (h.status == kDone) {
+      w.state = PSL_DONE;
+      w.t_done = t;
+      ctx->active_dirty = true;
+    } else if (h.status == kError) {
+      w.state = PSL_ERROR;
+      w.error = (int32_t)h.error;
+      w.t_done = t;
+      ctx->active_dirty = true;
+    }
+  }
+  return PSL_OK;
+}
+
+static cudaError_t enqueue_batched_step(psl_ctx *ctx, const LaunchCtx &c, bool timed) {
+  cudaError_t (*fns[5])(const LaunchCtx &) = {launch_hot_batched, launch_select, launch_recheck, launch_decide,
+                                               launch_apply};
+  const int kinds[5] = {kPHot, kPSelect, kPRecheck, kPDecide, kPApply};
+  for (int q = 0; q < 5; q++) {
+    cudaError_t e = timed ? prof_begin(ctx, kinds[q]) : cudaSuccess;
+    if (e == cudaSuccess) e = fns[q](c);
+    if (e == cudaSuccess && timed) e = prof_end(ctx);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+static int run_batched(psl_ctx *ctx, uint32_t steps) {
+  if (ctx->active.empty() || steps == 0) return PSL_OK;
+  LaunchCtx c = launch_ctx(ctx, ctx->d_active, (uint32_t)ctx->active.size());
+  const uint32_t G = (uint32_t)ctx->cfg.steps_per_graph;
+  uint32_t done = 0;
+  if (G > 0) {
+    if (!ctx->graph || ctx->graph_steps != G) {
+      if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+      ctx->graph = nullptr;
+      cudaGraph_t g;
+      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t e = cudaSuccess;
+      for (uint32_t t = 0; t < G && e == cudaSuccess; t++) e = enqueue_batched_step(ctx, c, false);
+      cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+      if (e != cudaSuccess || e2 != cudaSuccess)
+        return fail(ctx, PSL_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+      e = cudaGraphInstantiate(&ctx->graph, g, 0);
+      cudaGraphDestroy(g);
+      if (e != cudaSuccess) return fail(ctx, PSL_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+      ctx->graph_steps = G;
+    }
+    while (steps - done >= G) {
+      CK(prof_begin(ctx, kPGraph));
+      CK(cudaGraphLaunch(ctx->graph, ctx->stream));
+      CK(prof_end(ctx));
+      done += G;
+    }
+  }
+  for (; done < steps; done++) {
+    cudaError_t e = enqueue_batched_step(ctx, c, true);
+    if (e != cudaSuccess) return fail(ctx, PSL_ECUDA, "step launch: %s", cudaGetErrorString(e));
+  }
+  return PSL_OK;
+}
+
+// Host-side selection of the plain form: the same rule as k_select.
+static void host_select(const WalkDev &h, const std::vector<float> &score, const std::vector<int32_t> &pslj,
+                        std::vector<uint32_t> &cand, float *m_out, double *B_out, int32_t *win_psl,
+                        uint32_t *win_i) {
+  const uint32_t N = h.N;
+  float m = 3.4028234663852886e38f;
+  for (uint32_t i = 0; i < N; i++) m = std::min(m, score[i]);
+  const double B = score_bound(h.S_abs, h.alpha, h.L);
+  const double td = (double)m + 2.0 * B;
+  float thr = (float)td;
+  if ((double)thr < td) thr = std::nextafter(thr, 3.4e38f);  // round up
+  cand.clear();
+  for (uint32_t i = 0; i < N; i++)
+    if (score[i] <= thr) cand.push_back(i + 1);
+  const uint32_t topk = std::min<uint32_t>(h.topk, 16u);
+  if (cand.size() < topk) {
+    std::vector<std::pair<float, uint32_t>> rest;
+    for (uint32_t i = 0; i < N; i++)
+      if (!(score[i] <= thr)) rest.push_back({score[i], i + 1});
+    std::sort(rest.begin(), rest.end());
+    for (size_t r = 0; r < rest.size() && cand.size() < topk; r++) cand.push_back(rest[r].second);
+    std::sort(cand.begin(), cand.end());
+  }
+  *m_out = m;
+  *B_out = B;
+  *win_psl = INT32_MAX;
+  *win_i = 0;
+  if (h.ktau_on) {
+    for (uint32_t i = 0; i < N; i++)
+      if (pslj[i] < *win_psl) {
+        *win_psl = pslj[i];
+        *win_i = i + 1;
+      }
+  }
+}
+
+static int run_plain(psl_ctx *ctx, uint32_t steps) {
+  std::vector<float> score;
+  std::vector<int32_t> pslj;
+  std::vector<uint32_t> cand;
+  for (uint32_t s : ctx->active) {
+    WalkDev *dh = ctx->d_hdr + s;
+    uint32_t list_host = s;
+    CK(cudaMemcpyAsync(ctx->d_active, &list_host, sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+    LaunchCtx c = launch_ctx(ctx, ctx->d_active, 1);
+    c.max_chunk_apply = ctx->h_hdr[s].nchunk_apply;
+    c.max_chunk_rc = ctx->h_hdr[s].nchunk_rc;
+    for (uint32_t t = 0; t < steps; t++) {
+      WalkDev h;
+      CK(cudaMemcpyAsync(&h, dh, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      if (h.status != kRunning) break;
+      CK(prof_begin(ctx, kPHotPlain));
+      cudaError_t e = launch_hot_plain(dh, h.N, ctx->stream);
+      if (e != cudaSuccess) return fail(ctx, PSL_ECUDA, "plain kernel: %s", cudaGetErrorString(e));
+      CK(prof_end(ctx));
+      score.resize(h.N);
+      pslj.resize(h.N);
+      CK(cudaMemcpyAsync(score.data(), h.score, 4 * h.N, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaMemcpyAsync(pslj.data(), h.pslj, 4 * h.N, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      float m;
+      double B;
+      int32_t wp;
+      uint32_t wi;
+      host_select(h, score, pslj, cand, &m, &B, &wp, &wi);
+      const uint32_t n = (uint32_t)cand.size();
+      const float bf = (float)B;
+      CK(cudaMemcpyAsync(h.cand, cand.data(), 4 * n, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync((char *)dh + offsetof(WalkDev, ncand), &n, 4, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync((char *)dh + offsetof(WalkDev, score_min), &m, 4, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync((char *)dh + offsetof(WalkDev, bound), &bf, 4, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync((char *)dh + offsetof(WalkDev, win_psl), &wp, 4, cudaMemcpyHostToDevice, ctx->stream));
+      CK(cudaMemcpyAsync((char *)dh + offsetof(WalkDev, win_psl_i), &wi, 4, cudaMemcpyHostToDevice, ctx->stream));
+      CK(prof_begin(ctx, kPRecheck));
+      e = launch_recheck(c);
+      if (e == cudaSuccess) e = prof_end(ctx);
+      if (e == cudaSuccess) e = prof_begin(ctx, kPDecide);
+      if (e == cudaSuccess) e = launch_decide(c);
+      if (e == cudaSuccess) e = prof_end(ctx);
+      if (e == cudaSuccess) e = prof_begin(ctx, kPApply);
+      if (e == cudaSuccess) e = launch_apply(c);
+      if (e == cudaSuccess) e = prof_end(ctx);
+      if (e != cudaSuccess) return fail(ctx, PSL_ECUDA, "plain step: %s", cudaGetErrorString(e));
+      CK(cudaStreamSynchronize(ctx->stream));  // host buffers above are reused next step
+      prof_collect(ctx);
+    }
+  }
+  return PSL_OK;
+}
+
+extern "C" int psl_step(psl_ctx *ctx, uint32_t max_moves) {
+  if (!ctx) return PSL_EINVAL;
+  CK(cudaSetDevice(ctx->cfg.device));
+  int rc = admit(ctx);
+  if (rc) return rc;
+  if (ctx->active_dirty) {
+    rc = rebuild_active(ctx);
+    if (rc) return rc;
+  }
+  // never run past the largest remaining budget
+  uint64_t remaining = 0;
+  for (uint32_t s : ctx->active) {
+    const WalkDev &h = ctx->h_hdr[s];
+    uint64_t done = h.moves;
+    remaining = std::max<uint64_t>(remaining, h.budget > done ? h.budget - done : 0);
+  }
+  const uint32_t steps = (uint32_t)std::min<uint64_t>(max_moves, remaining);
+  rc = ctx->cfg.form == PSL_FORM_PLAIN ? run_plain(ctx, steps) : run_batched(ctx, steps);
+  if (rc) return rc;
+  rc = refresh_headers(ctx);
+  if (rc) return rc;
+  int n = (int)ctx->queue.size();
+  for (auto &kv : ctx->walks) n += kv.second.state == PSL_RUNNING;
+  return n;
+}
+
+static HostWalk *find(psl_ctx *ctx, int64_t id) {
+  auto it = ctx->walks.find(id);
+  return it == ctx->walks.end() ? nullptr : &it->second;
+}
+
+static double limbs_to_double(const uint32_t *a) {
+  // correctly rounded conversion of a two's-complement 384-bit value
+  uint32_t m[kWideLimbs];
+  std::memcpy(m, a, sizeof m);
+  const bool neg = m[kWideLimbs - 1] >> 31;
+  if (neg) {
+    uint64_t carry = 1;
+    for (int i = 0; i < kWideLimbs; i++) {
+      const uint64_t v = (uint64_t)(uint32_t)~m[i] + carry;
+      m[i] = (uint32_t)v;
+      carry = v >> 32;
+    }
+  }
+  int top = -1;
+  for (int i = 32 * kWideLimbs - 1; i >= 0; i--)
+    if ((m[i >> 5] >> (i & 31)) & 1u) {
+      top = i;
+      break;
+    }
+  if (top < 0) return 0.0;
+  auto bit = [&](int i) -> uint64_t { return (m[i >> 5] >> (i & 31)) & 1u; };
+  double r;
+  if (top <= 52) {
+    r = (double)(((uint64_t)m[1] << 32) | m[0]);
+  } else {
+    const int drop = top - 52;
+    uint64_t mant = 0;
+    for (int i = top; i >= drop; i--) mant = (mant << 1) | bit(i);
+    const uint64_t rnd = bit(drop - 1);
+    uint64_t sticky = 0;
+    for (int i = drop - 2; i >= 0; i--) sticky |= bit(i);
+    if (rnd && (sticky || (mant & 1u))) mant++;
+    r = std::ldexp((double)mant, drop);
+  }
+  return neg ? -r : r;
+}
+
+extern "C" int psl_poll(psl_ctx *ctx, int64_t id, psl_status *out) {
+  if (!ctx || !out) return PSL_EINVAL;
+  HostWalk *w = find(ctx, id);
+  if (!w) return PSL_ENOENT;
+  std::memset(out, 0, sizeof *out);
+  out->state = w->state;
+  out->error = w->error;
+  out->L = w->p.L;
+  out->t_submit = w->t_submit;
+  out->t_start = w->t_start;
+  out->t_done = w->t_done;
+  if (w->slot >= 0) {
+    const WalkDev &h = ctx->h_hdr[w->slot];
+    out->alpha = h.alpha;
+    out->moves = h.moves;
+    out->flip_evals = h.flip_evals;
+    out->switches = h.switches;
+    out->rechecks = h.rechecks;
+    out->psl = h.psl;
+    out->psl_best = h.psl_best;
+    out->unimproved = h.unimproved;
+    out->F = limbs_to_double(h.F);
+    out->value_local = limbs_to_double(h.value_local);
+  } else {
+    out->alpha = (uint32_t)w->p.alpha1;
+  }
+  return PSL_OK;
+}
+
+static int download_pm1(psl_ctx *ctx, const uint32_t *dbits, uint32_t L, int8_t *out) {
+  std::vector<uint32_t> words((L + 31) / 32);
+  CK(cudaMemcpyAsync(words.data(), dbits, words.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  for (uint32_t i = 0; i < L; i++) out[i] = ((words[i >> 5] >> (i & 31)) & 1u) ? -1 : 1;
+  return PSL_OK;
+}
+
+extern "C" int psl_best(psl_ctx *ctx, int64_t id, int32_t *psl_out, int8_t *seq, size_t cap) {
+  if (!ctx) return PSL_EINVAL;
+  HostWalk *w = find(ctx, id);
+  if (!w) return PSL_ENOENT;
+  if (w->slot < 0) return PSL_EBUSY;
+  if (seq && cap < w->p.L) return fail(ctx, PSL_EINVAL, "cap %zu < L %u", cap, w->p.L);
+  const WalkDev &h = ctx->h_hdr[w->slot];
+  if (psl_out) *psl_out = h.psl_best;
+  if (seq) return download_pm1(ctx, h.bits_best, w->p.L, seq);
+  return PSL_OK;
+}
+
+extern "C" int psl_release(psl_ctx *ctx, int64_t id) {
+  if (!ctx) return PSL_EINVAL;
+  HostWalk *w = find(ctx, id);
+  if (!w) return PSL_ENOENT;
+  if (w->state == PSL_QUEUED) {
+    ctx->queue.erase(std::remove(ctx->queue.begin(), ctx->queue.end(), id), ctx->queue.end());
+  } else if (w->slot >= 0) {
+    CK(cudaStreamSynchronize(ctx->stream));
+    WalkDev z{};
+    z.status = kFree;
+    CK(cudaMemcpy(ctx->d_hdr + w->slot, &z, sizeof z, cudaMemcpyHostToDevice));
+    ctx->h_hdr[w->slot] = z;
+    ctx->alloc.release(w->off, w->bytes);
+    ctx->free_slots.push_back(w->slot);
+    if (w->state == PSL_RUNNING) ctx->active_dirty = true;
+  }
+  ctx->walks.erase(id);
+  return PSL_OK;
+}
+
+extern "C" int psl_export_state(psl_ctx *ctx, int64_t id, psl_walk_state *st, int8_t *pivot, int8_t *local_best,
+                                int8_t *sol_best, int32_t *C, size_t cap) {
+  if (!ctx) return PSL_EINVAL;
+  HostWalk *w = find(ctx, id);
+  if (!w) return PSL_ENOENT;
+  if (w->slot < 0) return PSL_EBUSY;
+  const uint32_t L = w->p.L;
+  if ((pivot || local_best || sol_best || C) && cap < L) return fail(ctx, PSL_EINVAL, "cap < L");
+  WalkDev h;
+  CK(cudaMemcpyAsync(&h, ctx->d_hdr + w->slot, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (st) {
+    std::memset(st, 0, sizeof *st);
+    st->L = h.L;
+    st->N = h.N;
+    st->alpha = h.alpha;
+    st->unimproved = h.unimproved;
+    st->psl = h.psl;
+    st->psl_best = h.psl_best;
+    st->psl_local = h.psl_local;
+    st->start = h.start;
+    st->rng_ctr = h.rng_ctr;
+    st->moves = h.moves;
+    std::memcpy(st->F, h.F, sizeof st->F);
+    std::memcpy(st->value_local, h.value_local, sizeof st->value_local);
+    st->state = w->state;
+  }
+  int rc = PSL_OK;
+  if (pivot && (rc = download_pm1(ctx, h.bits, L, pivot))) return rc;
+  if (local_best && (rc = download_pm1(ctx, h.bits_local, L, local_best))) return rc;
+  if (sol_best && (rc = download_pm1(ctx, h.bits_best, L, sol_best))) return rc;
+  if (C) {
+    CK(cudaMemcpyAsync(C, h.C, (size_t)L * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return PSL_OK;
+}
+
+extern "C" int psl_trace(psl_ctx *ctx, int64_t id, psl_trace_rec *out, size_t cap) {
+  if (!ctx || (!out && cap)) return PSL_EINVAL;
+  HostWalk *w = find(ctx, id);
+  if (!w) return PSL_ENOENT;
+  if (w->slot < 0) return PSL_EBUSY;
+  static_assert(sizeof(psl_trace_rec) == sizeof(TraceRec), "trace record layout");
+  const WalkDev &h = ctx->h_hdr[w->slot];
+  const uint64_t n = std::min<uint64_t>(std::min<uint64_t>(h.moves, h.trace_cap), cap);
+  if (n) {
+    CK(cudaMemcpyAsync(out, h.trace, n * sizeof(TraceRec), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+  }
+  return (int)n;
+}
+
+extern "C" int psl_autocorr(psl_ctx *ctx, const int8_t *seq, uint32_t nseq, uint32_t L, int32_t *C) {
+  if (!ctx || !seq || !C || nseq == 0 || L < 1 || L > (1u << 20) - 1u) return PSL_EINVAL;
+  // runs as init-only walks in temporary slots of a private header array
+  const uint32_t nw = (L + 31) / 32;
+  const size_t words = nw + 2 * kGuardWords;
+  const size_t per = align_up(words * 4, 256) * 3 + align_up((size_t)L * 4, 256);
+  char *buf = nullptr;
+  WalkDev *dh = nullptr;
+  uint32_t *dl = nullptr;
+  CK(cudaMalloc(&buf, per * nseq));
+  std::vector<WalkDev> hh(nseq);
+  std::vector<uint32_t> list(nseq);
+  std::vector<uint32_t> packed;
+  int rc = PSL_OK;
+  cudaError_t e = cudaSuccess;
+  for (uint32_t q = 0; q < nseq && e == cudaSuccess; q++) {
+    WalkDev &h = hh[q];
+    std::memset(&h, 0, sizeof h);
+    char *b = buf + per * q;
+    h.L = L;
+    h.nw = nw;
+    h.has_init_seq = 1;
+    h.bits = (uint32_t *)b + kGuardWords;
+    h.bits_local = (uint32_t *)(b + align_up(words * 4, 256)) + kGuardWords;
+    h.bits_best = (uint32_t *)(b + 2 * align_up(words * 4, 256)) + kGuardWords;
+    h.C = (int32_t *)(b + 3 * align_up(words * 4, 256));
+    h.status = kRunning;
+    list[q] = q;
+    pack_pm1(seq + (size_t)q * L, L, packed);
+    e = cudaMemcpy(h.bits, packed.data(), packed.size() * 4, cudaMemcpyHostToDevice);
+  }
+  if (e == cudaSuccess) e = cudaMalloc(&dh, sizeof(WalkDev) * nseq);
+  if (e == cudaSuccess) e = cudaMalloc(&dl, sizeof(uint32_t) * nseq);
+  if (e == cudaSuccess) e = cudaMemcpy(dh, hh.data(), sizeof(WalkDev) * nseq, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(dl, list.data(), sizeof(uint32_t) * nseq, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    LaunchCtx c{};
+    c.hdr = dh;
+    c.active = dl;
+    c.nactive = nseq;
+    c.max_chunk_apply = (L + kApplyChunk - 1) / kApplyChunk;
+    c.stream = ctx->stream;
+    e = launch_init_bits(c);
+    if (e == cudaSuccess) e = launch_autocorr(c, L);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+  }
+  for (uint32_t q = 0; q < nseq && e == cudaSuccess; q++)
+    e = cudaMemcpy(C + (size_t)q * L, hh[q].C, (size_t)L * 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) rc = fail(ctx, PSL_ECUDA, "psl_autocorr: %s", cudaGetErrorString(e));
+  cudaFree(buf);
+  if (dh) cudaFree(dh);
+  if (dl) cudaFree(dl);
+  return rc;
+}

@@ -1,0 +1,257 @@
+"""Parity of the CUDA path (through the C-ABI) with the CPU oracle.
+
+Bar: bit-exact C_k, PSL, chosen moves, psl_best / solution_best and exact F;
+the FP64 value of F equals the correctly rounded exact value (so it is within
+1e-12 of the oracle's FP64 value by construction)."""
+import numpy as np
+import pytest
+
+import oracle as O
+import psl_workloads as W
+from helpers import (compare_final_state, compare_traces, fft_autocorr, have_gpu, limbs32_to_int, oracle_walk,
+                     parallel_eval, submit_spec)
+
+pytestmark = [pytest.mark.gpu, pytest.mark.skipif(not have_gpu(), reason="needs a CUDA GPU")]
+
+ARENA = 6 << 30
+
+
+@pytest.fixture(scope="module")
+def P():
+    from paper_2107_09801_gb300 import build
+    build.build()
+    import paper_2107_09801_gb300 as P
+    return P
+
+
+def run_gpu(P, specs, form="batched", init_seqs=None, **ctx_kw):
+    with P.Context(form=form, arena_bytes=ctx_kw.pop("arena_bytes", ARENA), max_walks=max(8, len(specs)),
+                   **ctx_kw) as ctx:
+        ids = [submit_spec(ctx, s, init_seq=None if init_seqs is None else init_seqs[i]) for i, s in enumerate(specs)]
+        ctx.run()
+        out = []
+        for i, s in zip(ids, specs):
+            assert ctx.poll(i)["state"] == P.PSL_DONE
+            out.append((ctx.trace(i, s.budget), ctx.export_state(i), ctx.poll(i), ctx.best(i)))
+        return out
+
+
+# ------------------------------------------------------------------------------------------------
+# a0: autocorrelation
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("L", [2, 3, 13, 31, 32, 33, 63, 64, 65, 1000, 4095])
+def test_autocorr_matches_oracle(P, L):
+    seqs = np.stack([W.random_pm1(L, 100 * L + r) for r in range(3)])
+    with P.Context(arena_bytes=1 << 24, max_walks=8) as ctx:
+        C = ctx.autocorr(seqs)
+    for r in range(3):
+        assert np.array_equal(C[r], O.autocorr(seqs[r]))
+
+
+@pytest.mark.parametrize("L", [131071, 1048575])
+def test_autocorr_full_size_matches_fft(P, L):
+    s = W.random_pm1(L, L)
+    with P.Context(arena_bytes=1 << 26, max_walks=8) as ctx:
+        C = ctx.autocorr(s)[0]
+    assert np.array_equal(C.astype(np.int64), fft_autocorr(s))
+
+
+# ------------------------------------------------------------------------------------------------
+# whole trajectories: a1..a6 through the C-ABI, step by step against the oracle
+# ------------------------------------------------------------------------------------------------
+SMALL = W.small_specs(seed=7, count=10)
+
+
+@pytest.mark.parametrize("form", ["batched", "plain"])
+def test_trajectories_match_oracle(P, form):
+    res = run_gpu(P, SMALL, form=form)
+    for spec, (tr, st, pl, best) in zip(SMALL, res):
+        w = oracle_walk(spec)
+        otr = w.run(spec.budget)
+        label = f"{form} L={spec.L} seed={spec.seed} a={spec.alpha1}/{spec.alpha2} N={spec.N} ls={spec.ls_lmt}"
+        compare_traces(tr, otr, label)
+        compare_final_state(st, w, label)
+        assert best[0] == w.psl_best and np.array_equal(best[1], w.sol_best)
+        assert pl["F"] == float(w.F) and pl["moves"] == spec.budget
+        assert pl["flip_evals"] == spec.budget * spec.N
+
+
+def test_phase_switches_are_exercised(P):
+    specs = [W.WalkSpec(L=L, seed=3 + L, alpha1=3, alpha2=11, n_lmt=nl, ls_lmt=2, flip_lmt=fl, budget=150)
+             for L, nl, fl in ((31, 31, 4), (127, 40, 10), (255, 6912, 7), (500, 100, 10))]
+    res = run_gpu(P, specs)
+    for spec, (tr, st, pl, _) in zip(specs, res):
+        w = oracle_walk(spec)
+        otr = w.run(spec.budget)
+        compare_traces(tr, otr, f"L={spec.L}")
+        compare_final_state(st, w)
+        assert pl["switches"] >= 3
+
+
+@pytest.mark.parametrize("L", [2, 3, 4, 5, 7])
+def test_tiny_lengths(P, L):
+    specs = [W.WalkSpec(L=L, seed=s, alpha1=1 + s % 5, alpha2=16, n_lmt=L, ls_lmt=1, flip_lmt=1 + s % L, budget=30)
+             for s in range(3)]
+    res = run_gpu(P, specs)
+    for spec, (tr, st, _, _) in zip(specs, res):
+        w = oracle_walk(spec)
+        compare_traces(tr, w.run(spec.budget), f"L={L}")
+        compare_final_state(st, w)
+
+
+def test_explicit_start_sequence(P, golden):
+    (row,) = golden("barker13.txt")
+    barker = np.array([1 if ch == "+" else -1 for ch in row], dtype=np.int8)
+    rnd = W.random_pm1(700, 1)
+    specs = [W.WalkSpec(L=13, seed=5, n_lmt=13, ls_lmt=3, budget=40),
+             W.WalkSpec(L=700, seed=9, n_lmt=250, ls_lmt=20, budget=60)]
+    res = run_gpu(P, specs, init_seqs=[barker, rnd])
+    for spec, s0, (tr, st, _, best) in zip(specs, (barker, rnd), res):
+        w = oracle_walk(spec, s0=s0)
+        compare_traces(tr, w.run(spec.budget))
+        compare_final_state(st, w)
+    assert res[0][3][0] == 1   # Barker-13 stays the best solution (PSL 1)
+
+
+def test_plain_form_matches_paper_window(P):
+    """L = 1023 with the full neighbourhood (N = L), seed 1, alpha 4/13, 2000 moves."""
+    spec = W.plain_small().walks[0]
+    w = oracle_walk(spec)
+    otr = w.run(spec.budget)
+    for form in ("batched", "plain"):
+        (tr, st, pl, _), = run_gpu(P, [spec], form=form)
+        compare_traces(tr, otr, form)
+        compare_final_state(st, w, form)
+
+
+def test_graph_capture_matches_launches(P):
+    specs = W.small_specs(seed=11, count=6)
+    a = run_gpu(P, specs, steps_per_graph=0)
+    b = run_gpu(P, specs, steps_per_graph=8)
+    for (ta, sa, _, _), (tb, sb, _, _) in zip(a, b):
+        assert ta.tobytes() == tb.tobytes()
+        assert np.array_equal(sa["C"], sb["C"])
+
+
+# ------------------------------------------------------------------------------------------------
+# batching: the same walk alone and in a mix gives the same result
+# ------------------------------------------------------------------------------------------------
+def test_batch_composition_invariance(P):
+    specs = W.small_specs(seed=3, count=8, L_choices=(31, 255, 1023, 4095))
+    mixed = run_gpu(P, specs)
+    for spec, (tr, st, _, _) in zip(specs, mixed):
+        (tr1, st1, _, _), = run_gpu(P, [spec])
+        assert tr.tobytes() == tr1.tobytes()
+        assert np.array_equal(st["C"], st1["C"]) and np.array_equal(st["pivot"], st1["pivot"])
+
+
+def test_continuous_admission_matches_alone(P):
+    """Walks submitted while others are on the GPU, admitted as memory frees up."""
+    specs = [W.WalkSpec(L=L, seed=100 + r, alpha1=2 + r % 4, alpha2=9 + r % 5, budget=20 + 7 * r, ls_lmt=5)
+             for r, L in enumerate([1023, 4095, 255, 16383, 511, 2047, 8191, 127])]
+    big = max(P.psl_walk_bytes(s.L, s.n_lmt, s.budget) for s in specs)
+    with P.Context(arena_bytes=3 * big, max_walks=4) as ctx:   # room for about three walks at once
+        ids, pending, results = {}, list(specs), {}
+        while pending or len(results) < len(ids):
+            if pending:
+                s = pending.pop(0)
+                ids[submit_spec(ctx, s)] = s
+            ctx.step(5)
+            for i, s in list(ids.items()):
+                if i not in results and ctx.poll(i)["state"] == P.PSL_DONE:
+                    results[i] = (ctx.trace(i, s.budget), ctx.export_state(i))
+                    ctx.release(i)
+        assert len(results) == len(specs)
+    for i, s in ids.items():
+        w = oracle_walk(s)
+        compare_traces(results[i][0], w.run(s.budget), f"L={s.L}")
+        compare_final_state(results[i][1], w)
+
+
+# ------------------------------------------------------------------------------------------------
+# full sizes, in the launch configuration the benchmark times, checked on sampled outputs
+# ------------------------------------------------------------------------------------------------
+def _check_full_size(P, wl, steps, n_check, full_window=False, sample=48):
+    specs = list(wl.walks)
+    with P.Context(arena_bytes=int(1.3 * sum(P.psl_walk_bytes(s.L, s.n_lmt, steps) for s in specs)) + (1 << 28),
+                   max_walks=len(specs)) as ctx:
+        ids = [submit_spec(ctx, W.with_budget(s, steps)) for s in specs]
+        # state before the last step, for the decision check
+        ctx.step(steps - 1)
+        pre = {}
+        rng = np.random.Generator(np.random.PCG64(1))
+        check = sorted(rng.choice(len(specs), size=n_check, replace=False).tolist())
+        for q in check:
+            pre[q] = ctx.export_state(ids[q])
+        ctx.step(1)
+        for q in check:
+            spec, wid = specs[q], ids[q]
+            tr = ctx.trace(wid, steps)
+            st = ctx.export_state(wid)
+            s = st["pivot"]
+            C = fft_autocorr(s)
+            assert np.array_equal(st["C"].astype(np.int64), C)                 # C_k of the pivot (Eq. 2)
+            assert st["psl"] == int(np.abs(C[1:]).max())                      # PSL (Eq. 3)
+            Fx, _, _ = O.fitness(st["C"], st["alpha"])
+            assert st["F"] == Fx                                              # exact F (Eq. 4)
+            # the last decision: k* minimises the exact F over the window (first in scan order)
+            p = pre[q]
+            last = tr[-1]
+            L, N = spec.L, spec.N
+            assert last["start"] == p["start"]
+            window = [(p["start"] + i) % L for i in range(1, N + 1)]
+            if full_window:
+                js = window
+            else:
+                js = sorted(set(rng.choice(window, size=min(sample, N), replace=False).tolist()) | {int(last["kstar"])})
+            vals, psls = parallel_eval(p["pivot"], p["C"], p["alpha"], js)
+            pos = {j: n for n, j in enumerate(window)}
+            kv = vals[js.index(int(last["kstar"]))]
+            assert kv == limbs32_to_int(last["value_exact"])
+            for j, v in zip(js, vals):
+                assert v > kv or (v == kv and pos[j] >= pos[int(last["kstar"])]), (q, j)
+            if full_window and last["win_psl"] != 2**31 - 1:
+                assert last["win_psl"] == psls.min()
+
+
+def test_full_size_L16383_x4096(P):
+    _check_full_size(P, W.batch_16383(), steps=2, n_check=2, full_window=True)
+
+
+def test_full_size_L131071_x1024(P):
+    _check_full_size(P, W.batch_131071(), steps=2, n_check=2)
+
+
+def test_full_size_L1048575_x148(P):
+    _check_full_size(P, W.batch_1048575(), steps=1 + 1, n_check=1, sample=24)
+
+
+# ------------------------------------------------------------------------------------------------
+# error behaviour of the boundary
+# ------------------------------------------------------------------------------------------------
+def test_argument_errors(P):
+    with P.Context(arena_bytes=1 << 22, max_walks=2) as ctx:
+        for bad in [dict(L=1), dict(L=1 << 20), dict(alpha1=0), dict(alpha2=17), dict(budget=0)]:
+            kw = dict(L=100, seed=1, alpha1=4, alpha2=13, budget=10)
+            kw.update(bad)
+            with pytest.raises(P.PslError) as e:
+                ctx.submit_ex(kw["L"], kw["seed"], kw["alpha1"], kw["alpha2"], kw["budget"])
+            assert e.value.code == -1
+        with pytest.raises(P.PslError) as e:
+            ctx.submit(100, 1, 4.5, 13, 10)
+        assert e.value.code == -1
+        with pytest.raises(P.PslError) as e:
+            ctx.submit(1048575, 1, 4, 13, 10)      # needs far more than the 4 MB arena
+        assert e.value.code == -2
+        with pytest.raises(P.PslError) as e:
+            ctx.poll(12345)
+        assert e.value.code == -3
+        wid = ctx.submit(100, 1, 4, 13, 10)
+        with pytest.raises(P.PslError) as e:
+            ctx.best(wid)                            # still queued
+        assert e.value.code == -4
+        ctx.run()
+        assert ctx.poll(wid)["state"] == P.PSL_DONE
+        ctx.release(wid)
+        with pytest.raises(P.PslError):
+            ctx.poll(wid)
