@@ -6,6 +6,7 @@
 // F = sum_{k>=1} |C_k|^alpha (Eq. 4).  A "window" is the limited neighbourhood of
 // Algorithm 1: N = min(N_lmt, L) neighbours j = (start + i) % L, i = 1..N.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -33,10 +34,11 @@ struct TraceRec {
   int32_t psl, psl_best, win_psl;
   uint32_t win_psl_j, flags, nflip, ncand;
   float score_kstar, score_min, bound;
-  uint32_t pad;
+  uint32_t pad[2];                // explicit: value_step starts at byte 72, no implicit padding
   double value_step;              // exact F of the chosen neighbour, rounded to FP64
   uint32_t value_exact[kWideLimbs];
 };
+static_assert(sizeof(TraceRec) == 128 && offsetof(TraceRec, value_step) == 72, "trace record layout");
 
 // One walk slot.  Static fields are written by the host at admission; dynamic
 // fields are owned by the device while the walk runs.
