@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     return ap.parse_args()
 
 
@@ -107,44 +108,42 @@ class ClockSampler:
 # ------------------------------------------------------------------------------------------------
 # the oracle on the host cores (reference arm and cpu_baseline)
 # ------------------------------------------------------------------------------------------------
-def oracle_rate(L: int, n_lmt: int, alpha: int, seconds: float, threads: int | None = None):
-    """Flip-evals/s of the oracle's neighbour evaluation (exact F and PSL of each
-    neighbour, Eq. 2-4 through the one-element flip) on `threads` host threads, each on
-    its own walk, over a bounded sample of window positions sized to about `seconds`."""
-    import numpy as np
+class OracleSampler:
+    """Times the oracle's neighbour evaluation (exact F and PSL of each neighbour, Eq. 2-4
+    through the one-element flip of Sec. 3) on `threads` host threads, each on its own walk
+    of length L, over bounded samples of the walk's window."""
 
-    import oracle as O
+    def __init__(self, L: int, n_lmt: int, alpha: int, threads: int | None = None):
+        import oracle as O
+        self.O, self.L, self.n_lmt, self.alpha = O, L, n_lmt, alpha
+        self.threads = threads or os.cpu_count() or 1
+        self.walks = [None] * self.threads
 
-    threads = threads or os.cpu_count() or 1
-    walks = [None] * threads
+        def init(r):
+            self.walks[r] = O.Walk(O.WalkParams(L=L, seed=r, alpha1=alpha, alpha2=13, n_lmt=n_lmt))
 
-    def init(r):
-        walks[r] = O.Walk(O.WalkParams(L=L, seed=r, alpha1=alpha, alpha2=13, n_lmt=n_lmt))
+        ts = [threading.Thread(target=init, args=(r,)) for r in range(self.threads)]
+        [t.start() for t in ts]
+        [t.join() for t in ts]
+        w0 = self.walks[0]
+        t0 = time.perf_counter()
+        O.eval_neighbours(w0.s, w0.C, alpha, [1, 2])
+        self.per = max((time.perf_counter() - t0) / 2, 1e-5)
 
-    ts = [threading.Thread(target=init, args=(r,)) for r in range(threads)]
-    [t.start() for t in ts]
-    [t.join() for t in ts]
-    # calibrate on one neighbour, then size the per-thread sample
-    w0 = walks[0]
-    t0 = time.perf_counter()
-    O.eval_neighbours(w0.s, w0.C, alpha, [1])
-    per = max(time.perf_counter() - t0, 1e-4)
-    n_per = int(max(1, min(n_lmt, seconds / per)))
-    counts = [0] * threads
+    def sample(self, seconds: float):
+        n_per = int(max(1, min(self.n_lmt, seconds / self.per)))
 
-    def work(r):
-        w = walks[r]
-        start = O.splitmix64(w.p.seed, w.rng_ctr) % L
-        js = [(start + i) % L for i in range(1, n_per + 1)]
-        O.eval_neighbours(w.s, w.C, alpha, js)
-        counts[r] = len(js)
+        def work(r):
+            w = self.walks[r]
+            start = self.O.splitmix64(w.p.seed, w.rng_ctr) % self.L
+            self.O.eval_neighbours(w.s, w.C, self.alpha, [(start + i) % self.L for i in range(1, n_per + 1)])
 
-    ts = [threading.Thread(target=work, args=(r,)) for r in range(threads)]
-    t0 = time.perf_counter()
-    [t.start() for t in ts]
-    [t.join() for t in ts]
-    dt = time.perf_counter() - t0
-    return sum(counts) / dt, threads, n_per, dt
+        ts = [threading.Thread(target=work, args=(r,)) for r in range(self.threads)]
+        t0 = time.perf_counter()
+        [t.start() for t in ts]
+        [t.join() for t in ts]
+        dt = time.perf_counter() - t0
+        return self.threads * n_per / dt, n_per, dt
 
 
 def run_reference(args):
@@ -152,15 +151,16 @@ def run_reference(args):
     if rank != 0:
         return 0
     L, N = 131071, W.N_LMT
-    threads = os.cpu_count() or 1
+    sampler = OracleSampler(L, N, 4)
     # each step: every host thread evaluates a bounded slice of its walk's window
     per_step_s = max(0.5, min(6.0, 150.0 / max(1, args.steps + args.warmup)))
     vals = []
     for s in range(args.warmup + args.steps):
-        v, cores, n_per, dt = oracle_rate(L, N, 4, per_step_s, threads)
+        v, n_per, dt = sampler.sample(per_step_s)
         if s >= args.warmup:
             vals.append((v, dt, n_per))
     value = statistics.median(v for v, _, _ in vals)
+    cores = sampler.threads
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * statistics.median(d for _, d, _ in vals),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i384 exact (oracle)",
@@ -216,7 +216,7 @@ def run_ours(args):
     specs = [W.WalkSpec(L=s.L, seed=s.seed + rank * args.walks, alpha1=s.alpha1, alpha2=s.alpha2, budget=s.budget)
              for s in wl.walks]
     L, N = specs[0].L, specs[0].N
-    assert args.warmup + args.steps <= specs[0].budget
+    assert args.warmup + args.steps <= specs[0].budget and args.warmup >= 1
     need = sum(P.psl_walk_bytes(s.L, s.n_lmt, 0) for s in specs)
     arena = torch.empty(int(need * 1.1) + (64 << 20), dtype=torch.uint8, device=dev)
 
@@ -229,7 +229,9 @@ def run_ours(args):
     out = {}
     with P.Context(arena_tensor=arena, stream=stream, max_walks=len(specs), device=local) as ctx:
         ids = [ctx.submit(s.L, s.seed, s.alpha1, s.alpha2, s.budget) for s in specs]
-        ctx.step(args.warmup)   # admission, initialisation and warm-up steps
+        ctx.step(1)             # admission and initialisation
+        tuned = ctx.autotune(reps=2) if not args.no_autotune else None
+        ctx.step(args.warmup - 1)
         barrier()
         clk = ClockSampler(local)
         clk.start()
@@ -283,7 +285,8 @@ def run_ours(args):
     if not args.no_e2e:
         barrier()
         t0 = time.perf_counter()
-        with P.Context(arena_tensor=arena, stream=stream, max_walks=len(specs), device=local) as ctx:
+        hot = dict(hot_threads=tuned[0], hot_tile_sb=tuned[1]) if tuned else {}
+        with P.Context(arena_tensor=arena, stream=stream, max_walks=len(specs), device=local, **hot) as ctx:
             ids = [ctx.submit(s.L, s.seed, s.alpha1, s.alpha2, s.budget) for s in specs]
             ctx.step(args.steps)
             psl_sum = 0
@@ -308,6 +311,7 @@ def run_ours(args):
                 "data": "synthetic",
                 "config": {"workload": wl.name, "L": L, "walks_per_gpu": len(specs), "n_lmt": N, "alpha": "4/13",
                            "ls_lmt": W.LS_LMT, "flip_lmt": W.FLIP_LMT, "form": "batched",
+                           "hot_kernel": {"threads": tuned[0], "tile_superblocks": tuned[1]} if tuned else "default",
                            "l2": "inputs larger than L2 (walk state %.1f GB per GPU)" % (need / 1e9)},
                 "roofline": {"bound": "alu", "kernel": "k_hot_batched", "achieved": achieved / 1e12,
                              "peak": peak / 1e12, "unit": "Tops/s", "frac": achieved / peak,
@@ -321,7 +325,9 @@ def run_ours(args):
                 "paper_context": {"A100_one_walk_flip_evals_per_s_L131071": PAPER_A100_L131071},
                 "e2e": e2e}
         if not args.no_cpu_baseline:
-            v, cores, n_per, dt = oracle_rate(L, N, 4, args.cpu_sample_s)
+            sampler = OracleSampler(L, N, 4)
+            v, n_per, dt = sampler.sample(args.cpu_sample_s)
+            cores = sampler.threads
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                     "sample": f"{cores} threads x {n_per} window neighbours of their own L=131071 "
                                               f"walk, exact F and PSL each ({dt:.1f} s)"}

@@ -84,8 +84,9 @@ typedef struct {
   void *stream;             /* cudaStream_t for all work; NULL = library-owned stream */
   int32_t form;             /* PSL_FORM_BATCHED or PSL_FORM_PLAIN                     */
   int32_t max_walks;        /* number of walk slots                                   */
-  int32_t hot_tile_sb;      /* k-tile of the batched kernel, super-blocks of 30 k; 0 = auto */
+  int32_t hot_tile_sb;      /* k-tile of the batched kernel in super-blocks of 30 k: 16 or 32; 0 = auto */
   int32_t steps_per_graph;  /* steps captured per CUDA graph launch; 0 = plain launches */
+  int32_t hot_threads;      /* neighbours per block of the batched kernel: 128, 256 or 512; 0 = auto */
 } psl_config;
 
 /* Per-walk parameters of psl_submit_ex.  n_lmt, flip_lmt <= 0 and ls_lmt < 0 take
@@ -205,6 +206,19 @@ PSL_API int psl_profile(psl_ctx *ctx, int enable);
 
 /* Copies up to cap per-kernel totals; returns the number of kernel families. */
 PSL_API int psl_profile_read(psl_ctx *ctx, psl_kernel_time *out, size_t cap);
+
+/* Autotuner of the batched form: admits queued walks, then times every supported
+ * configuration of the neighbourhood kernel (neighbours per block 128/256/512 x k-tile
+ * of 16/32 super-blocks, which sets the shared-memory footprint) on the walks now
+ * running, reps launches each, and keeps the fastest for this context.  The timed
+ * launches only recompute window scores that the next step recomputes, so no result
+ * changes.  Returns threads | (tile_sb << 16) of the choice, PSL_ESTATE when no walk
+ * is running, PSL_EINVAL for the plain form or reps < 1. */
+PSL_API int psl_autotune(psl_ctx *ctx, int reps);
+
+/* Sets the neighbourhood-kernel configuration of the batched form directly (for a
+ * choice cached from an earlier psl_autotune).  PSL_EINVAL for unsupported values. */
+PSL_API int psl_set_hot_config(psl_ctx *ctx, int32_t threads, int32_t tile_sb);
 
 /* Destroys the context and frees its device memory.  NULL is ignored. */
 PSL_API void psl_shutdown(psl_ctx *ctx);

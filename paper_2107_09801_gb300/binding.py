@@ -25,7 +25,8 @@ class PslError(RuntimeError):
 class psl_config(ct.Structure):
     _fields_ = [("n_lmt", ct.c_int32), ("ls_lmt", ct.c_int32), ("flip_lmt", ct.c_int32), ("device", ct.c_int32),
                 ("arena_bytes", ct.c_uint64), ("arena", ct.c_void_p), ("stream", ct.c_void_p), ("form", ct.c_int32),
-                ("max_walks", ct.c_int32), ("hot_tile_sb", ct.c_int32), ("steps_per_graph", ct.c_int32)]
+                ("max_walks", ct.c_int32), ("hot_tile_sb", ct.c_int32), ("steps_per_graph", ct.c_int32),
+                ("hot_threads", ct.c_int32)]
 
 
 class psl_walk_params(ct.Structure):
@@ -63,7 +64,7 @@ assert TRACE_DTYPE.itemsize == 128  # psl_trace_rec has no implicit padding
 
 EXPORTED = ["psl_config_default", "psl_init", "psl_submit", "psl_submit_ex", "psl_step", "psl_poll", "psl_best",
             "psl_release", "psl_export_state", "psl_trace", "psl_autocorr", "psl_walk_bytes", "psl_shutdown",
-            "psl_last_error", "psl_profile", "psl_profile_read"]
+            "psl_last_error", "psl_profile", "psl_profile_read", "psl_autotune", "psl_set_hot_config"]
 
 _lib = None
 
@@ -98,6 +99,8 @@ def lib():
             "psl_last_error": (ct.c_char_p, [P]),
             "psl_profile": (ct.c_int, [P, ct.c_int]),
             "psl_profile_read": (ct.c_int, [P, ct.POINTER(psl_kernel_time), ct.c_size_t]),
+            "psl_autotune": (ct.c_int, [P, ct.c_int]),
+            "psl_set_hot_config": (ct.c_int, [P, ct.c_int32, ct.c_int32]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -210,6 +213,23 @@ def psl_shutdown(ctx) -> None:
     lib().psl_shutdown(ctx)
 
 
+def psl_autotune(ctx, reps: int = 3) -> tuple[int, int]:
+    r = _check(ctx, lib().psl_autotune(ctx, reps))
+    return r & 0xFFFF, r >> 16
+
+
+def psl_set_hot_config(ctx, threads: int, tile_sb: int) -> None:
+    _check(ctx, lib().psl_set_hot_config(ctx, threads, tile_sb))
+
+
+def _gpu_name() -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name()
+    except Exception:
+        return "unknown-gpu"
+
+
 def psl_profile(ctx, enable: bool) -> None:
     _check(ctx, lib().psl_profile(ctx, 1 if enable else 0))
 
@@ -227,11 +247,12 @@ class Context:
 
     def __init__(self, *, form: str = "batched", arena_bytes: int = 0, arena_tensor=None, stream=None,
                  max_walks: int = 4096, n_lmt: int = 6912, ls_lmt: int = 2000, flip_lmt: int = 10, device: int = 0,
-                 hot_tile_sb: int = 0, steps_per_graph: int = 0):
+                 hot_tile_sb: int = 0, steps_per_graph: int = 0, hot_threads: int = 0):
         cfg = psl_config_default()
         cfg.n_lmt, cfg.ls_lmt, cfg.flip_lmt, cfg.device = n_lmt, ls_lmt, flip_lmt, device
         cfg.form = PSL_FORM_PLAIN if form == "plain" else PSL_FORM_BATCHED
         cfg.max_walks, cfg.hot_tile_sb, cfg.steps_per_graph = max_walks, hot_tile_sb, steps_per_graph
+        cfg.hot_threads = hot_threads
         self._arena_tensor = arena_tensor
         if arena_tensor is not None:
             cfg.arena = arena_tensor.data_ptr()
@@ -282,6 +303,34 @@ class Context:
 
     def autocorr(self, seqs) -> np.ndarray:
         return psl_autocorr(self.h, seqs)
+
+    def autotune(self, reps: int = 3, cache: str | None = None) -> tuple[int, int]:
+        """Picks the neighbourhood-kernel configuration for the running walks.  With a
+        cache file, a previous choice for the same GPU and length bucket is reused."""
+        key = None
+        if cache:
+            import json
+            Ls = [L for w, L in self.L_of.items()]
+            key = f"{_gpu_name()}|L<=2^{max(Ls).bit_length() if Ls else 0}|walks>={1 << max(len(Ls), 1).bit_length() >> 1}"
+            try:
+                table = json.load(open(cache))
+            except Exception:
+                table = {}
+            if key in table:
+                t, sb = table[key]
+                self._set_hot(t, sb)
+                return t, sb
+        t, sb = psl_autotune(self.h, reps)
+        if cache:
+            table[key] = [t, sb]
+            tmp = cache + ".tmp"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache)
+        return t, sb
+
+    def _set_hot(self, threads: int, tile_sb: int) -> None:
+        psl_set_hot_config(self.h, threads, tile_sb)
 
     def profile(self, enable: bool = True) -> None:
         psl_profile(self.h, enable)

@@ -110,6 +110,7 @@ cudaError_t launch_recheck(const LaunchCtx &c);
 cudaError_t launch_decide(const LaunchCtx &c);
 cudaError_t launch_start_init(const LaunchCtx &c);
 size_t hot_batched_smem(uint32_t tile_sb);
+bool hot_config_supported(uint32_t threads, uint32_t tile_sb);  // block sizes 128/256/512, tiles 16/32
 
 // Candidate threshold shared bit-for-bit by the device select and the host select
 // of the plain form.  Returns the largest FP32 score that may still belong to the

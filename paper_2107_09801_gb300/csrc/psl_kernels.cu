@@ -482,61 +482,112 @@ __global__ void __launch_bounds__(256) k_apply(WalkDev *hdr, const uint32_t *act
 //   both partners present:  delta = +4 if u=v=1, -4 if u=v=0, else 0
 //   one partner present:    delta = +2 if its bit is 1, else -2
 // (k <= kin = min(j, L-1-j): both present; kin < k <= kout = max(j, L-1-j): one; beyond: none.)
-// k is processed in super-blocks of 30 = 6 groups of 5.  For each group the block keeps
-// three 32-entry subset-sum tables in shared memory:
-//   W1[b] = sum_{q in b} Tp4_q,  W0[b] = sum_{q in b} Tm4_q,  E[b] = sum_q (b_q ? Tp2_q : Tm2_q)
-// so one lookup scores five (j, k) terms.  Entry b of the tables of group g is stored at
-// position b ^ (g & 31) so that the per-thread build is free of bank conflicts.
+// k runs in super-blocks of 30 = 6 groups of 5.  For each group the block keeps three
+// 32-entry subset-sum tables in shared memory,
+//   W1[b] = sum_{q in b} Tp4_q,  W0[b] = sum_{q in b} Tm4_q,  E[b] = sum_q (b_q ? Tp2_q : Tm2_q),
+// so one lookup scores five (j, k) terms.  Super-block sb owns 2304 bytes (6 groups x 3
+// tables x 32 floats, 128-byte aligned) and entry b of all its tables sits at b ^ (sb & 31):
+// the build (one thread per group, consecutive lanes on consecutive super-blocks) is free
+// of bank conflicts, and a lookup address is ((W >> s) & 0x7C) ^ (base_sb | swizzle) plus a
+// constant: one shift and one three-input logic op.  Regions are decided per warp and per
+// super-block, so the common case runs without per-group tests.
 // ------------------------------------------------------------------------------------
-constexpr int kTabFloats = 96;  // 3 tables x 32 entries per group
+constexpr int kSbFloats = 576;           // 6 groups x 3 tables x 32 entries
+constexpr int kSbBytes = kSbFloats * 4;  // 2304 bytes = 18 x 128
 
-size_t hot_batched_smem(uint32_t tile_sb) { return (size_t)tile_sb * 6 * kTabFloats * sizeof(float); }
+// tables (rounded up to a 128-byte boundary inside the allocation) + one int
+size_t hot_batched_smem(uint32_t tile_sb) { return (size_t)tile_sb * kSbBytes + 256; }
 
-__device__ __forceinline__ void build_group_tables(float *tab, int g, const float4 *T, int kg, int L) {
+template <int OFF>
+__device__ __forceinline__ float lds_at(uint32_t addr) {
+  float v;
+  asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(OFF));
+  return v;
+}
+
+// 5-bit field Q of w, times 4 (a byte offset in bits 2..6)
+template <int Q>
+__device__ __forceinline__ uint32_t field4(uint32_t w) {
+  if constexpr (Q == 0)
+    return (w << 2) & 0x7Cu;
+  else
+    return (w >> (5 * Q - 2)) & 0x7Cu;
+}
+
+__device__ __forceinline__ uint32_t window32_ro(const uint32_t *__restrict__ bits, int pos) {
+  const int w = pos >> 5;
+  return __funnelshift_r(__ldg(bits + w), __ldg(bits + w + 1), pos & 31);
+}
+
+// tables of group q of super-block sb of the tile (first k of the group: kg)
+__device__ __forceinline__ void build_group(float *tab, int sb, int q, const float4 *__restrict__ T, int kg, int L) {
   float tp4[5], tm4[5], tp2[5], tm2[5];
 #pragma unroll
-  for (int q = 0; q < 5; q++) {
-    const int k = kg + q;
-    float4 t = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (k < L) t = T[k];
-    tp4[q] = t.x;
-    tm4[q] = t.y;
-    tp2[q] = t.z;
-    tm2[q] = t.w;
+  for (int t = 0; t < 5; t++) {
+    const int k = kg + t;
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (k < L) v = __ldg(T + k);
+    tp4[t] = v.x;
+    tm4[t] = v.y;
+    tp2[t] = v.z;
+    tm2[t] = v.w;
   }
-  const int sw = g & 31;
-  float *w1 = tab + g * kTabFloats, *w0 = w1 + 32, *ee = w1 + 64;
-  // low two bits and high three bits summed separately: every entry is a tree of depth 3
+  // low two bits and high three bits summed separately: every entry is a tree of depth <= 3
   float lo1[4], lo0[4], loe[4], hi1[8], hi0[8], hie[8];
+  lo1[0] = 0.f, lo1[1] = tp4[0], lo1[2] = tp4[1], lo1[3] = tp4[0] + tp4[1];
+  lo0[0] = 0.f, lo0[1] = tm4[0], lo0[2] = tm4[1], lo0[3] = tm4[0] + tm4[1];
+#pragma unroll
+  for (int b = 0; b < 4; b++) loe[b] = ((b & 1) ? tp2[0] : tm2[0]) + ((b & 2) ? tp2[1] : tm2[1]);
+  {
+    const float a23 = tp4[2] + tp4[3], b23 = tm4[2] + tm4[3];
+    hi1[0] = 0.f, hi1[1] = tp4[2], hi1[2] = tp4[3], hi1[3] = a23;
+    hi1[4] = tp4[4], hi1[5] = tp4[2] + tp4[4], hi1[6] = tp4[3] + tp4[4], hi1[7] = a23 + tp4[4];
+    hi0[0] = 0.f, hi0[1] = tm4[2], hi0[2] = tm4[3], hi0[3] = b23;
+    hi0[4] = tm4[4], hi0[5] = tm4[2] + tm4[4], hi0[6] = tm4[3] + tm4[4], hi0[7] = b23 + tm4[4];
+  }
 #pragma unroll
   for (int b = 0; b < 4; b++) {
-    lo1[b] = ((b & 1) ? tp4[0] : 0.f) + ((b & 2) ? tp4[1] : 0.f);
-    lo0[b] = ((b & 1) ? tm4[0] : 0.f) + ((b & 2) ? tm4[1] : 0.f);
-    loe[b] = ((b & 1) ? tp2[0] : tm2[0]) + ((b & 2) ? tp2[1] : tm2[1]);
+    const float p = ((b & 1) ? tp2[2] : tm2[2]) + ((b & 2) ? tp2[3] : tm2[3]);
+    hie[b] = p + tm2[4];
+    hie[b + 4] = p + tp2[4];
   }
-#pragma unroll
-  for (int b = 0; b < 8; b++) {
-    hi1[b] = (((b & 1) ? tp4[2] : 0.f) + ((b & 2) ? tp4[3] : 0.f)) + ((b & 4) ? tp4[4] : 0.f);
-    hi0[b] = (((b & 1) ? tm4[2] : 0.f) + ((b & 2) ? tm4[3] : 0.f)) + ((b & 4) ? tm4[4] : 0.f);
-    hie[b] = (((b & 1) ? tp2[2] : tm2[2]) + ((b & 2) ? tp2[3] : tm2[3])) + ((b & 4) ? tp2[4] : tm2[4]);
-  }
+  float *base = tab + sb * kSbFloats + q * 96;
+  const int sw = sb & 31;
 #pragma unroll
   for (int b = 0; b < 32; b++) {
-    w1[b ^ sw] = lo1[b & 3] + hi1[b >> 2];
-    w0[b ^ sw] = lo0[b & 3] + hi0[b >> 2];
-    ee[b ^ sw] = loe[b & 3] + hie[b >> 2];
+    const int lo = b & 3, hi = b >> 2;
+    base[b ^ sw] = lo == 0 ? hi1[hi] : (hi == 0 ? lo1[lo] : lo1[lo] + hi1[hi]);
+    base[32 + (b ^ sw)] = lo == 0 ? hi0[hi] : (hi == 0 ? lo0[lo] : lo0[lo] + hi0[hi]);
+    base[64 + (b ^ sw)] = loe[lo] + hie[hi];
   }
 }
 
 // exact per-term contribution used where a group straddles a region boundary
-__device__ __forceinline__ float term_slow(const float4 *T, int k, int kin, int kout, uint32_t U, uint32_t V,
-                                           bool plus_side, int t) {
+__device__ __forceinline__ float term_slow(const float4 *__restrict__ T, int k, int kin, int kout, uint32_t U,
+                                           uint32_t V, bool plus_side, int t) {
   if (k > kout) return 0.f;
-  const float4 tv = T[k];
+  const float4 tv = __ldg(T + k);
   const uint32_t u = (U >> t) & 1u, v = (V >> t) & 1u;
   if (k <= kin) return (u & v) ? tv.x : ((u | v) ? 0.f : tv.y);
   const uint32_t e = plus_side ? u : v;
   return e ? tv.z : tv.w;
+}
+
+// one group of a super-block where lanes may sit in different regions
+template <int Q>
+__device__ __forceinline__ void group_generic(float &a0, float &a1, uint32_t bsw, uint32_t W1, uint32_t W0,
+                                              uint32_t E, uint32_t U, uint32_t V, int ka, int kin, int kout,
+                                              bool plus_side, const float4 *__restrict__ T) {
+  const int kg = ka + 5 * Q;
+  if (kg + 4 <= kin) {
+    a0 += lds_at<Q * 384>(field4<Q>(W1) ^ bsw);
+    a1 += lds_at<Q * 384 + 128>(field4<Q>(W0) ^ bsw);
+  } else if (kg > kin && kg + 4 <= kout) {
+    a0 += lds_at<Q * 384 + 256>(field4<Q>(E) ^ bsw);
+  } else if (kg <= kout) {
+#pragma unroll
+    for (int t = 0; t < 5; t++) a1 += term_slow(T, kg + t, kin, kout, U, V, plus_side, 5 * Q + t);
+  }
 }
 
 // Exact neighbour PSL over the near-peak list: max_k |C_k + delta_jk| for |C_k| >= PSL - 8.
@@ -555,66 +606,101 @@ __device__ __forceinline__ int neighbour_psl(const WalkDev &W, const int2 *list,
   return cur;
 }
 
-__global__ void __launch_bounds__(256) k_hot_batched(WalkDev *hdr, const HotItem *items, uint32_t tile_sb) {
-  extern __shared__ float tab[];
-  __shared__ int s_kmax;
+template <int NT, int NSB>
+__global__ void __launch_bounds__(NT) k_hot_batched(WalkDev *hdr, const HotItem *items) {
+  extern __shared__ __align__(128) float smem_raw[];
+  const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(smem_raw);
+  const uint32_t tab_s = (raw_s + 127u) & ~127u;  // lookups OR a swizzle into the low 7 bits
+  float *tab = smem_raw + (tab_s - raw_s) / 4;
+  int *s_kmax = reinterpret_cast<int *>(tab + NSB * kSbFloats);
   const HotItem it = items[blockIdx.x];
   WalkDev &W = hdr[it.slot];
   if (W.status != kRunning) return;
   const int L = (int)W.L, N = (int)W.N;
-  const uint32_t *bits = W.bits;
-  const float4 *T = W.T;
+  const uint32_t *__restrict__ bits = W.bits;
+  const float4 *__restrict__ T = W.T;
   const int i = (int)it.i0 + (int)threadIdx.x;  // window position, 1-based
   const bool live = i <= N;
   const int j = (int)(((uint64_t)W.start + (uint64_t)i) % (uint64_t)L);
   const int kin = min(j, L - 1 - j), kout = live ? max(j, L - 1 - j) : 0;
   const bool plus_side = j < L - 1 - j;
   const uint32_t M = getbit(bits, j) ? 0xffffffffu : 0u;
-  const int cap_u = 32 * (int)W.nw, floor_v = -64;
-
-  if (threadIdx.x == 0) s_kmax = 0;
+  const int cap_u = 32 * (int)W.nw;
+  // warp-uniform region bounds (lanes past the window do not constrain them)
+  const int w_kin_lo = (int)__reduce_min_sync(0xffffffffu, (unsigned)(live ? kin : INT_MAX));
+  const int w_kin_hi = __reduce_max_sync(0xffffffffu, live ? kin : -1);
+  const int w_kout_lo = (int)__reduce_min_sync(0xffffffffu, (unsigned)(live ? kout : INT_MAX));
+  const int w_kout_hi = __reduce_max_sync(0xffffffffu, kout);
+  if (threadIdx.x == 0) *s_kmax = 0;
   __syncthreads();
-  {
-    const int km = warp_max(kout);
-    if ((threadIdx.x & 31) == 0) atomicMax(&s_kmax, km);
-  }
+  if ((threadIdx.x & 31) == 0) atomicMax(s_kmax, w_kout_hi);
   __syncthreads();
-  const int kmax = s_kmax;
-  const int tileK = (int)tile_sb * kSbK;
+  const int kmax = *s_kmax;
 
-  float hi = 0.f, lo = 0.f, blk = 0.f;
-  for (int kt0 = 1; kt0 <= kmax; kt0 += tileK) {
+  float hi = 0.f, lo = 0.f, a0 = 0.f, a1 = 0.f;
+  for (int kt0 = 1; kt0 <= kmax; kt0 += NSB * kSbK) {
     __syncthreads();  // previous tile fully consumed
-    const int ngroups = (int)tile_sb * 6;
-    for (int g = threadIdx.x; g < ngroups; g += blockDim.x) build_group_tables(tab, g, T, kt0 + 5 * g, L);
-    __syncthreads();
-    if (live && kt0 <= kout) {
-      for (int sb = 0; sb < (int)tile_sb; sb++) {
-        const int ka = kt0 + sb * kSbK;
-        if (ka > kout) break;
-        const uint32_t U = window32(bits, min(j + ka, cap_u)) ^ M;
-        const uint32_t V = __brev(window32(bits, max(j - ka - 31, floor_v))) ^ M;
-        const uint32_t W1 = U & V, W0 = ~(U | V), E = plus_side ? U : V;
-#pragma unroll
-        for (int q = 0; q < 6; q++) {
-          const int kg = ka + 5 * q;
-          const int g = sb * 6 + q;
-          const int sw = g & 31;
-          const float *tb = tab + g * kTabFloats;
-          if (kg + 4 <= kin) {
-            blk += tb[((W1 >> (5 * q)) & 31u) ^ sw];
-            blk += tb[32 + (((W0 >> (5 * q)) & 31u) ^ sw)];
-          } else if (kg > kin && kg + 4 <= kout) {
-            blk += tb[64 + (((E >> (5 * q)) & 31u) ^ sw)];
-          } else if (kg <= kout) {
-#pragma unroll
-            for (int t = 0; t < 5; t++) blk += term_slow(T, kg + t, kin, kout, U, V, plus_side, 5 * q + t);
-          }
-        }
-        if (sb & 1) flush_block(hi, lo, blk);
-      }
-      flush_block(hi, lo, blk);
+    for (int t = threadIdx.x; t < 6 * NSB; t += NT) {
+      const int sb = t % NSB, q = t / NSB;
+      build_group(tab, sb, q, T, kt0 + sb * kSbK + 5 * q, L);
     }
+    __syncthreads();
+    if (kt0 > w_kout_hi) continue;
+#pragma unroll 1
+    for (int sb = 0; sb < NSB; sb++) {
+      const int ka = kt0 + sb * kSbK;
+      if (ka > w_kout_hi) break;
+      const uint32_t bsw = (tab_s + (uint32_t)(sb * kSbBytes)) | ((uint32_t)(sb & 31) << 2);
+      if (ka + kSbK - 1 <= w_kin_lo) {
+        // every lane: both partners present for all 30 shifts
+        // (clamps only matter for lanes past the end of the window, whose sums are discarded)
+        const uint32_t U = window32_ro(bits, min(j + ka, cap_u));
+        const uint32_t V = __brev(window32_ro(bits, max(j - ka - 31, -64)));
+        const uint32_t W1 = (U ^ M) & (V ^ M), W0 = ~((U ^ M) | (V ^ M));
+        a0 += lds_at<0 * 384>(field4<0>(W1) ^ bsw);
+        a1 += lds_at<0 * 384 + 128>(field4<0>(W0) ^ bsw);
+        a0 += lds_at<1 * 384>(field4<1>(W1) ^ bsw);
+        a1 += lds_at<1 * 384 + 128>(field4<1>(W0) ^ bsw);
+        a0 += lds_at<2 * 384>(field4<2>(W1) ^ bsw);
+        a1 += lds_at<2 * 384 + 128>(field4<2>(W0) ^ bsw);
+        a0 += lds_at<3 * 384>(field4<3>(W1) ^ bsw);
+        a1 += lds_at<3 * 384 + 128>(field4<3>(W0) ^ bsw);
+        a0 += lds_at<4 * 384>(field4<4>(W1) ^ bsw);
+        a1 += lds_at<4 * 384 + 128>(field4<4>(W0) ^ bsw);
+        a0 += lds_at<5 * 384>(field4<5>(W1) ^ bsw);
+        a1 += lds_at<5 * 384 + 128>(field4<5>(W0) ^ bsw);
+      } else if (ka > w_kin_hi && ka + kSbK - 1 <= w_kout_lo) {
+        // every lane: exactly one partner for all 30 shifts
+        const int pos = plus_side ? min(j + ka, cap_u) : max(j - ka - 31, -64);
+        const uint32_t w = window32_ro(bits, pos);
+        const uint32_t E = (plus_side ? w : __brev(w)) ^ M;
+        a0 += lds_at<0 * 384 + 256>(field4<0>(E) ^ bsw);
+        a1 += lds_at<1 * 384 + 256>(field4<1>(E) ^ bsw);
+        a0 += lds_at<2 * 384 + 256>(field4<2>(E) ^ bsw);
+        a1 += lds_at<3 * 384 + 256>(field4<3>(E) ^ bsw);
+        a0 += lds_at<4 * 384 + 256>(field4<4>(E) ^ bsw);
+        a1 += lds_at<5 * 384 + 256>(field4<5>(E) ^ bsw);
+      } else if (ka <= kout) {
+        // region boundaries inside this super-block for some lane: per-group decisions
+        const uint32_t U = window32_ro(bits, min(j + ka, cap_u)) ^ M;
+        const uint32_t V = __brev(window32_ro(bits, max(j - ka - 31, -64))) ^ M;
+        const uint32_t W1 = U & V, W0 = ~(U | V), E = plus_side ? U : V;
+        group_generic<0>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
+        group_generic<1>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
+        group_generic<2>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
+        group_generic<3>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
+        group_generic<4>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
+        group_generic<5>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
+      }
+      if (sb & 1) {
+        float blk = a0 + a1;
+        a0 = a1 = 0.f;
+        flush_block(hi, lo, blk);
+      }
+    }
+    float blk = a0 + a1;
+    a0 = a1 = 0.f;
+    flush_block(hi, lo, blk);
   }
   if (!live) return;
   W.score[i - 1] = hi + lo;
@@ -1069,13 +1155,31 @@ cudaError_t launch_apply(const LaunchCtx &c) {
   return cudaGetLastError();
 }
 
+using HotFn = void (*)(WalkDev *, const HotItem *);
+
+static HotFn hot_variant(uint32_t threads, uint32_t tile_sb) {
+  if (threads == 512) return tile_sb == 16 ? k_hot_batched<512, 16> : k_hot_batched<512, 32>;
+  if (threads == 128) return tile_sb == 16 ? k_hot_batched<128, 16> : k_hot_batched<128, 32>;
+  return tile_sb == 16 ? k_hot_batched<256, 16> : k_hot_batched<256, 32>;
+}
+
+bool hot_config_supported(uint32_t threads, uint32_t tile_sb) {
+  return (threads == 128 || threads == 256 || threads == 512) && (tile_sb == 16 || tile_sb == 32);
+}
+
 cudaError_t prepare_kernels() {
-  return cudaFuncSetAttribute(k_hot_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  for (uint32_t t : {128u, 256u, 512u})
+    for (uint32_t sb : {16u, 32u}) {
+      cudaError_t e = cudaFuncSetAttribute(hot_variant(t, sb), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)hot_batched_smem(sb));
+      if (e != cudaSuccess) return e;
+    }
+  return cudaSuccess;
 }
 
 cudaError_t launch_hot_batched(const LaunchCtx &c) {
-  const size_t smem = hot_batched_smem(c.hot_tile_sb);
-  k_hot_batched<<<c.nitems, c.hot_threads, smem, c.stream>>>(c.hdr, c.items, c.hot_tile_sb);
+  hot_variant(c.hot_threads, c.hot_tile_sb)<<<c.nitems, c.hot_threads, hot_batched_smem(c.hot_tile_sb), c.stream>>>(
+      c.hdr, c.items);
   return cudaGetLastError();
 }
 

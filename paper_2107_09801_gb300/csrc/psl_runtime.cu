@@ -236,6 +236,7 @@ extern "C" void psl_config_default(psl_config *cfg) {
   cfg->max_walks = 4096;
   cfg->hot_tile_sb = 0;
   cfg->steps_per_graph = 0;
+  cfg->hot_threads = 0;
 }
 
 extern "C" uint64_t psl_walk_bytes(uint32_t L, int32_t n_lmt, uint32_t trace_cap) {
@@ -255,13 +256,15 @@ extern "C" int psl_init(const psl_config *cfg_in, psl_ctx **out) {
   else
     psl_config_default(&cfg);
   if (cfg.n_lmt < 1 || cfg.ls_lmt < 0 || cfg.flip_lmt < 0 || cfg.flip_lmt > kMaxFlips || cfg.max_walks < 1 ||
-      (cfg.form != PSL_FORM_BATCHED && cfg.form != PSL_FORM_PLAIN) || cfg.hot_tile_sb < 0 || cfg.hot_tile_sb > 80 ||
-      cfg.steps_per_graph < 0)
+      (cfg.form != PSL_FORM_BATCHED && cfg.form != PSL_FORM_PLAIN) || cfg.steps_per_graph < 0 ||
+      !hot_config_supported(cfg.hot_threads ? (uint32_t)cfg.hot_threads : 256u,
+                            cfg.hot_tile_sb ? (uint32_t)cfg.hot_tile_sb : 32u))
     return fail(nullptr, PSL_EINVAL, "invalid psl_config field");
   if (cfg.arena && cfg.arena_bytes == 0) return fail(nullptr, PSL_EINVAL, "arena given without arena_bytes");
   psl_ctx *ctx = new psl_ctx();
   ctx->cfg = cfg;
   if (ctx->cfg.hot_tile_sb == 0) ctx->cfg.hot_tile_sb = 32;
+  if (ctx->cfg.hot_threads == 0) ctx->cfg.hot_threads = 256;
   auto bail = [&](int code) {
     psl_shutdown(ctx);
     return code;
@@ -445,7 +448,7 @@ static int rebuild_active(psl_ctx *ctx) {
   ctx->max_chunk_rc = 1;
   for (uint32_t s : ctx->active) {
     const WalkDev &h = ctx->h_hdr[s];
-    for (uint32_t i0 = 1; i0 <= h.N; i0 += 256) items.push_back(HotItem{s, i0});
+    for (uint32_t i0 = 1; i0 <= h.N; i0 += (uint32_t)ctx->cfg.hot_threads) items.push_back(HotItem{s, i0});
     ctx->max_chunk_apply = std::max(ctx->max_chunk_apply, h.nchunk_apply);
     ctx->max_chunk_rc = std::max(ctx->max_chunk_rc, h.nchunk_rc);
   }
@@ -481,7 +484,7 @@ static LaunchCtx launch_ctx(psl_ctx *ctx, const uint32_t *d_list, uint32_t n) {
   c.nitems = ctx->nitems;
   c.max_chunk_apply = ctx->max_chunk_apply;
   c.max_chunk_rc = ctx->max_chunk_rc;
-  c.hot_threads = 256;
+  c.hot_threads = (uint32_t)ctx->cfg.hot_threads;
   c.hot_tile_sb = (uint32_t)ctx->cfg.hot_tile_sb;
   c.stream = ctx->stream;
   return c;
@@ -956,4 +959,48 @@ extern "C" int psl_autocorr(psl_ctx *ctx, const int8_t *seq, uint32_t nseq, uint
   if (dh) cudaFree(dh);
   if (dl) cudaFree(dl);
   return rc;
+}
+
+extern "C" int psl_autotune(psl_ctx *ctx, int reps) {
+  if (!ctx || reps < 1 || ctx->cfg.form != PSL_FORM_BATCHED) return PSL_EINVAL;
+  CK(cudaSetDevice(ctx->cfg.device));
+  int rc = admit(ctx);
+  if (rc) return rc;
+  if (ctx->active_dirty && (rc = rebuild_active(ctx))) return rc;
+  if (ctx->active.empty()) return fail(ctx, PSL_ESTATE, "no running walk to tune on");
+  cudaEvent_t a, b;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  float best_ms = 3.4e38f;
+  int32_t best_t = ctx->cfg.hot_threads, best_sb = ctx->cfg.hot_tile_sb;
+  for (int32_t t : {128, 256, 512})
+    for (int32_t sb : {16, 32}) {
+      ctx->cfg.hot_threads = t;
+      ctx->cfg.hot_tile_sb = sb;
+      if ((rc = rebuild_active(ctx))) return rc;
+      LaunchCtx c = launch_ctx(ctx, ctx->d_active, (uint32_t)ctx->active.size());
+      CK(launch_hot_batched(c));  // warm-up
+      CK(cudaEventRecord(a, ctx->stream));
+      for (int r = 0; r < reps; r++) CK(launch_hot_batched(c));
+      CK(cudaEventRecord(b, ctx->stream));
+      CK(cudaEventSynchronize(b));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, a, b));
+      if (ms < best_ms) best_ms = ms, best_t = t, best_sb = sb;
+    }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  ctx->cfg.hot_threads = best_t;
+  ctx->cfg.hot_tile_sb = best_sb;
+  if ((rc = rebuild_active(ctx))) return rc;
+  return best_t | (best_sb << 16);
+}
+
+extern "C" int psl_set_hot_config(psl_ctx *ctx, int32_t threads, int32_t tile_sb) {
+  if (!ctx || threads < 0 || tile_sb < 0 || !hot_config_supported((uint32_t)threads, (uint32_t)tile_sb))
+    return PSL_EINVAL;
+  ctx->cfg.hot_threads = threads;
+  ctx->cfg.hot_tile_sb = tile_sb;
+  ctx->active_dirty = true;  // the block list depends on the block size
+  return PSL_OK;
 }

@@ -255,3 +255,32 @@ def test_argument_errors(P):
         ctx.release(wid)
         with pytest.raises(P.PslError):
             ctx.poll(wid)
+
+
+# ------------------------------------------------------------------------------------------------
+# configurations of the neighbourhood kernel and the autotuner leave every decision unchanged
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("threads,tile_sb", [(128, 16), (128, 32), (256, 16), (512, 16), (512, 32)])
+def test_hot_kernel_configurations_match_oracle(P, threads, tile_sb):
+    specs = W.small_specs(seed=21, count=6, L_choices=(63, 1000, 2047, 4095))
+    res = run_gpu(P, specs, hot_threads=threads, hot_tile_sb=tile_sb)
+    for spec, (tr, st, _, _) in zip(specs, res):
+        w = oracle_walk(spec)
+        compare_traces(tr, w.run(spec.budget), f"{threads}/{tile_sb} L={spec.L}")
+        compare_final_state(st, w)
+
+
+def test_autotune_keeps_results(P, tmp_path):
+    specs = W.small_specs(seed=5, count=5, L_choices=(1023, 4095, 8191))
+    with P.Context(arena_bytes=ARENA, max_walks=8) as ctx:
+        ids = [submit_spec(ctx, s) for s in specs]
+        ctx.step(3)
+        t, sb = ctx.autotune(reps=2, cache=str(tmp_path / "tune.json"))
+        assert (t, sb) in [(a, b) for a in (128, 256, 512) for b in (16, 32)]
+        assert ctx.autotune(cache=str(tmp_path / "tune.json")) == (t, sb)   # cached choice
+        ctx.run()
+        got = [(ctx.trace(i, s.budget), ctx.export_state(i)) for i, s in zip(ids, specs)]
+    for spec, (tr, st) in zip(specs, got):
+        w = oracle_walk(spec)
+        compare_traces(tr, w.run(spec.budget), f"L={spec.L}")
+        compare_final_state(st, w)
