@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--hot-threads", type=int, default=0, help="force the neighbourhood-kernel block size")
+    ap.add_argument("--hot-tile", type=int, default=0, help="force the k-tile (super-blocks of 30)")
     return ap.parse_args()
 
 
@@ -230,7 +232,11 @@ def run_ours(args):
     with P.Context(arena_tensor=arena, stream=stream, max_walks=len(specs), device=local) as ctx:
         ids = [ctx.submit(s.L, s.seed, s.alpha1, s.alpha2, s.budget) for s in specs]
         ctx.step(1)             # admission and initialisation
-        tuned = ctx.autotune(reps=2) if not args.no_autotune else None
+        if args.hot_threads or args.hot_tile:
+            ctx._set_hot(args.hot_threads or 256, args.hot_tile or 32)
+            tuned = (args.hot_threads or 256, args.hot_tile or 32)
+        else:
+            tuned = ctx.autotune(reps=2) if not args.no_autotune else None
         ctx.step(args.warmup - 1)
         barrier()
         clk = ClockSampler(local)
