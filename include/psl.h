@@ -220,6 +220,23 @@ PSL_API int psl_autotune(psl_ctx *ctx, int reps);
  * choice cached from an earlier psl_autotune).  PSL_EINVAL for unsupported values. */
 PSL_API int psl_set_hot_config(psl_ctx *ctx, int32_t threads, int32_t tile_sb);
 
+/* No counterpart in the paper.  For callers that must not allocate device memory
+ * themselves -- code running under another framework's allocator, where a raw cudaFree
+ * would synchronise the whole device, or services that reserve every buffer at start-up
+ * so that no later request can block or fail on an allocation: the autocorrelation of
+ * Eq. 2 for one sequence already in device memory, computed with a scratch area built
+ * into the library (128 KiB per device, held until the process exits) instead of
+ * allocating.  seq_dev: device array of L int8 values (negative means -1, anything else
+ * +1); C_dev: device array of L int32 receiving C_0..C_{L-1}; stream: a cudaStream_t or
+ * NULL.  Requires 1 <= L <= 2^20 - 1 (PSL_EINVAL otherwise, and for NULL pointers);
+ * PSL_ECUDA if the scratch lookup or a launch fails.  Calls no allocator.  Work is queued
+ * on the stream and the caller synchronises.  The first call on each device looks up the
+ * scratch address, so make that first call before any stream capture.  Every call on a
+ * device uses the same scratch, which keeps the previous call's contents (each call
+ * rewrites all of it that it reads): calls that can overlap on the GPU, such as calls on
+ * different streams with no ordering between them, race and give wrong results. */
+PSL_API int psl_autocorr_static(const int8_t *seq_dev, uint32_t L, int32_t *C_dev, void *stream);
+
 /* Destroys the context and frees its device memory.  NULL is ignored. */
 PSL_API void psl_shutdown(psl_ctx *ctx);
 

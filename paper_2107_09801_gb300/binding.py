@@ -64,7 +64,8 @@ assert TRACE_DTYPE.itemsize == 128  # psl_trace_rec has no implicit padding
 
 EXPORTED = ["psl_config_default", "psl_init", "psl_submit", "psl_submit_ex", "psl_step", "psl_poll", "psl_best",
             "psl_release", "psl_export_state", "psl_trace", "psl_autocorr", "psl_walk_bytes", "psl_shutdown",
-            "psl_last_error", "psl_profile", "psl_profile_read", "psl_autotune", "psl_set_hot_config"]
+            "psl_last_error", "psl_profile", "psl_profile_read", "psl_autotune", "psl_set_hot_config",
+            "psl_autocorr_static"]
 
 _lib = None
 
@@ -101,6 +102,7 @@ def lib():
             "psl_profile_read": (ct.c_int, [P, ct.POINTER(psl_kernel_time), ct.c_size_t]),
             "psl_autotune": (ct.c_int, [P, ct.c_int]),
             "psl_set_hot_config": (ct.c_int, [P, ct.c_int32, ct.c_int32]),
+            "psl_autocorr_static": (ct.c_int, [P, ct.c_uint32, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -203,6 +205,14 @@ def psl_autocorr(ctx, seqs: np.ndarray) -> np.ndarray:
     C = np.zeros((n, L), dtype=np.int32)
     _check(ctx, lib().psl_autocorr(ctx, _ptr(seqs), n, L, _ptr(C)))
     return C
+
+
+def psl_autocorr_static(seq_dev_ptr: int, L: int, C_dev_ptr: int, stream: int | None = None) -> None:
+    """Autocorrelation of one sequence in device memory with the library's built-in
+    scratch, for callers that cannot allocate device memory (see include/psl.h)."""
+    rc = lib().psl_autocorr_static(seq_dev_ptr, L, C_dev_ptr, stream)
+    if rc < 0:
+        raise PslError(rc, "psl_autocorr_static failed")
 
 
 def psl_walk_bytes(L: int, n_lmt: int = 6912, trace_cap: int = 0) -> int:
