@@ -606,8 +606,70 @@ __device__ __forceinline__ int neighbour_psl(const WalkDev &W, const int2 *list,
   return cur;
 }
 
+// One super-block where every lane has both partners for all 30 shifts.
+__device__ __forceinline__ void sb_interior(float &a0, float &a1, const uint32_t *__restrict__ bits, int pos_u,
+                                            int pos_v, uint32_t M, uint32_t bsw) {
+  const uint32_t U = window32_ro(bits, pos_u);
+  const uint32_t V = __brev(window32_ro(bits, pos_v));
+  const uint32_t W1 = (U ^ M) & (V ^ M), W0 = ~((U ^ M) | (V ^ M));
+  a0 += lds_at<0 * 384>(field4<0>(W1) ^ bsw);
+  a1 += lds_at<0 * 384 + 128>(field4<0>(W0) ^ bsw);
+  a0 += lds_at<1 * 384>(field4<1>(W1) ^ bsw);
+  a1 += lds_at<1 * 384 + 128>(field4<1>(W0) ^ bsw);
+  a0 += lds_at<2 * 384>(field4<2>(W1) ^ bsw);
+  a1 += lds_at<2 * 384 + 128>(field4<2>(W0) ^ bsw);
+  a0 += lds_at<3 * 384>(field4<3>(W1) ^ bsw);
+  a1 += lds_at<3 * 384 + 128>(field4<3>(W0) ^ bsw);
+  a0 += lds_at<4 * 384>(field4<4>(W1) ^ bsw);
+  a1 += lds_at<4 * 384 + 128>(field4<4>(W0) ^ bsw);
+  a0 += lds_at<5 * 384>(field4<5>(W1) ^ bsw);
+  a1 += lds_at<5 * 384 + 128>(field4<5>(W0) ^ bsw);
+}
+
+// One super-block where every lane has exactly one partner for all 30 shifts.
+__device__ __forceinline__ void sb_edge(float &a0, float &a1, const uint32_t *__restrict__ bits, int pos,
+                                        bool plus_side, uint32_t M, uint32_t bsw) {
+  const uint32_t w = window32_ro(bits, pos);
+  const uint32_t E = (plus_side ? w : __brev(w)) ^ M;
+  a0 += lds_at<0 * 384 + 256>(field4<0>(E) ^ bsw);
+  a1 += lds_at<1 * 384 + 256>(field4<1>(E) ^ bsw);
+  a0 += lds_at<2 * 384 + 256>(field4<2>(E) ^ bsw);
+  a1 += lds_at<3 * 384 + 256>(field4<3>(E) ^ bsw);
+  a0 += lds_at<4 * 384 + 256>(field4<4>(E) ^ bsw);
+  a1 += lds_at<5 * 384 + 256>(field4<5>(E) ^ bsw);
+}
+
+// One super-block where region boundaries fall inside it for some lane.
+__device__ __forceinline__ void sb_generic(float &a0, float &a1, const uint32_t *__restrict__ bits,
+                                           const float4 *__restrict__ T, int j, int ka, int kin, int kout,
+                                           bool plus_side, uint32_t M, uint32_t bsw, int cap_u) {
+  if (ka > kout) return;
+  const uint32_t U = window32_ro(bits, min(j + ka, cap_u)) ^ M;
+  const uint32_t V = __brev(window32_ro(bits, max(j - ka - 31, -64))) ^ M;
+  const uint32_t W1 = U & V, W0 = ~(U | V), E = plus_side ? U : V;
+  group_generic<0>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
+  group_generic<1>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
+  group_generic<2>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
+  group_generic<3>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
+  group_generic<4>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
+  group_generic<5>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
+}
+
+__device__ __forceinline__ void flush2(float &hi, float &lo, float &a0, float &a1) {
+  float blk = a0 + a1;
+  a0 = a1 = 0.f;
+  flush_block(hi, lo, blk);
+}
+
+// number of super-blocks sb >= 0 of a tile starting at kt0 with kt0 + 30 sb + off <= bound
+__device__ __forceinline__ int sb_count(int bound, int kt0, int off, int nsb) {
+  const int d = bound - kt0 - off;
+  return d < 0 ? 0 : min(nsb, d / kSbK + 1);
+}
+
 template <int NT, int NSB>
 __global__ void __launch_bounds__(NT) k_hot_batched(WalkDev *hdr, const HotItem *items) {
+  static_assert(NSB <= 32, "the per-super-block swizzle assumes at most 32 super-blocks per tile");
   extern __shared__ __align__(128) float smem_raw[];
   const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(smem_raw);
   const uint32_t tab_s = (raw_s + 127u) & ~127u;  // lookups OR a swizzle into the low 7 bits
@@ -621,16 +683,18 @@ __global__ void __launch_bounds__(NT) k_hot_batched(WalkDev *hdr, const HotItem 
   const float4 *__restrict__ T = W.T;
   const int i = (int)it.i0 + (int)threadIdx.x;  // window position, 1-based
   const bool live = i <= N;
-  const int j = (int)(((uint64_t)W.start + (uint64_t)i) % (uint64_t)L);
-  const int kin = min(j, L - 1 - j), kout = live ? max(j, L - 1 - j) : 0;
+  // lanes past the end of the window shadow the last neighbour (their sums are discarded),
+  // so every lane of a partly filled warp stays inside the regions of a real neighbour
+  const int j = (int)(((uint64_t)W.start + (uint64_t)min(i, N)) % (uint64_t)L);
+  const bool warp_live = (int)it.i0 + (int)(threadIdx.x & ~31u) <= N;
+  const int kin = min(j, L - 1 - j), kout = max(j, L - 1 - j);
   const bool plus_side = j < L - 1 - j;
   const uint32_t M = getbit(bits, j) ? 0xffffffffu : 0u;
   const int cap_u = 32 * (int)W.nw;
-  // warp-uniform region bounds (lanes past the window do not constrain them)
-  const int w_kin_lo = (int)__reduce_min_sync(0xffffffffu, (unsigned)(live ? kin : INT_MAX));
-  const int w_kin_hi = __reduce_max_sync(0xffffffffu, live ? kin : -1);
-  const int w_kout_lo = (int)__reduce_min_sync(0xffffffffu, (unsigned)(live ? kout : INT_MAX));
-  const int w_kout_hi = __reduce_max_sync(0xffffffffu, kout);
+  const int w_kin_lo = __reduce_min_sync(0xffffffffu, kin);
+  const int w_kin_hi = __reduce_max_sync(0xffffffffu, kin);
+  const int w_kout_lo = __reduce_min_sync(0xffffffffu, kout);
+  const int w_kout_hi = warp_live ? __reduce_max_sync(0xffffffffu, kout) : 0;
   if (threadIdx.x == 0) *s_kmax = 0;
   __syncthreads();
   if ((threadIdx.x & 31) == 0) atomicMax(s_kmax, w_kout_hi);
@@ -645,62 +709,56 @@ __global__ void __launch_bounds__(NT) k_hot_batched(WalkDev *hdr, const HotItem 
       build_group(tab, sb, q, T, kt0 + sb * kSbK + 5 * q, L);
     }
     __syncthreads();
-    if (kt0 > w_kout_hi) continue;
-#pragma unroll 1
-    for (int sb = 0; sb < NSB; sb++) {
-      const int ka = kt0 + sb * kSbK;
-      if (ka > w_kout_hi) break;
-      const uint32_t bsw = (tab_s + (uint32_t)(sb * kSbBytes)) | ((uint32_t)(sb & 31) << 2);
-      if (ka + kSbK - 1 <= w_kin_lo) {
-        // every lane: both partners present for all 30 shifts
-        // (clamps only matter for lanes past the end of the window, whose sums are discarded)
-        const uint32_t U = window32_ro(bits, min(j + ka, cap_u));
-        const uint32_t V = __brev(window32_ro(bits, max(j - ka - 31, -64)));
-        const uint32_t W1 = (U ^ M) & (V ^ M), W0 = ~((U ^ M) | (V ^ M));
-        a0 += lds_at<0 * 384>(field4<0>(W1) ^ bsw);
-        a1 += lds_at<0 * 384 + 128>(field4<0>(W0) ^ bsw);
-        a0 += lds_at<1 * 384>(field4<1>(W1) ^ bsw);
-        a1 += lds_at<1 * 384 + 128>(field4<1>(W0) ^ bsw);
-        a0 += lds_at<2 * 384>(field4<2>(W1) ^ bsw);
-        a1 += lds_at<2 * 384 + 128>(field4<2>(W0) ^ bsw);
-        a0 += lds_at<3 * 384>(field4<3>(W1) ^ bsw);
-        a1 += lds_at<3 * 384 + 128>(field4<3>(W0) ^ bsw);
-        a0 += lds_at<4 * 384>(field4<4>(W1) ^ bsw);
-        a1 += lds_at<4 * 384 + 128>(field4<4>(W0) ^ bsw);
-        a0 += lds_at<5 * 384>(field4<5>(W1) ^ bsw);
-        a1 += lds_at<5 * 384 + 128>(field4<5>(W0) ^ bsw);
-      } else if (ka > w_kin_hi && ka + kSbK - 1 <= w_kout_lo) {
-        // every lane: exactly one partner for all 30 shifts
-        const int pos = plus_side ? min(j + ka, cap_u) : max(j - ka - 31, -64);
-        const uint32_t w = window32_ro(bits, pos);
-        const uint32_t E = (plus_side ? w : __brev(w)) ^ M;
-        a0 += lds_at<0 * 384 + 256>(field4<0>(E) ^ bsw);
-        a1 += lds_at<1 * 384 + 256>(field4<1>(E) ^ bsw);
-        a0 += lds_at<2 * 384 + 256>(field4<2>(E) ^ bsw);
-        a1 += lds_at<3 * 384 + 256>(field4<3>(E) ^ bsw);
-        a0 += lds_at<4 * 384 + 256>(field4<4>(E) ^ bsw);
-        a1 += lds_at<5 * 384 + 256>(field4<5>(E) ^ bsw);
-      } else if (ka <= kout) {
-        // region boundaries inside this super-block for some lane: per-group decisions
-        const uint32_t U = window32_ro(bits, min(j + ka, cap_u)) ^ M;
-        const uint32_t V = __brev(window32_ro(bits, max(j - ka - 31, -64))) ^ M;
-        const uint32_t W1 = U & V, W0 = ~(U | V), E = plus_side ? U : V;
-        group_generic<0>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-        group_generic<1>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-        group_generic<2>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-        group_generic<3>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-        group_generic<4>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-        group_generic<5>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
+    // warp-uniform phases of this tile, in increasing k:
+    //   [0, n_int)        every lane interior        (ka + 29 <= min kin)
+    //   [n_int, e0)       generic                   (around the kin boundaries)
+    //   [e0, n_edge)      every lane one partner     (ka > max kin, ka + 29 <= min kout)
+    //   [n_edge, n_all)   generic                   (around the kout boundaries)
+    const int n_all = sb_count(w_kout_hi, kt0, 0, NSB);
+    const int n_int = min(sb_count(w_kin_lo, kt0, kSbK - 1, NSB), n_all);
+    const int e0 = max(n_int, min(n_all, sb_count(w_kin_hi, kt0, 0, NSB)));
+    const int n_edge = max(e0, min(n_all, sb_count(w_kout_lo, kt0, kSbK - 1, NSB)));
+    const uint32_t bsw0 = tab_s;  // super-block sb: base + 2304 sb, swizzle sb << 2
+    int sb = 0;
+    {
+      int pu = j + kt0, pv = j - kt0 - 31;
+      uint32_t bsw = bsw0;
+      for (; sb + 1 < n_int; sb += 2) {
+        sb_interior(a0, a1, bits, pu, pv, M, bsw);
+        sb_interior(a0, a1, bits, pu + kSbK, pv - kSbK, M, bsw + (kSbBytes + 4));
+        flush2(hi, lo, a0, a1);
+        pu += 2 * kSbK, pv -= 2 * kSbK, bsw += 2 * (kSbBytes + 4);
       }
-      if (sb & 1) {
-        float blk = a0 + a1;
-        a0 = a1 = 0.f;
-        flush_block(hi, lo, blk);
+      if (sb < n_int) {
+        sb_interior(a0, a1, bits, pu, pv, M, bsw);
+        flush2(hi, lo, a0, a1);
+        sb++;
       }
     }
-    float blk = a0 + a1;
-    a0 = a1 = 0.f;
-    flush_block(hi, lo, blk);
+    for (; sb < e0; sb++) {
+      sb_generic(a0, a1, bits, T, j, kt0 + sb * kSbK, kin, kout, plus_side, M, bsw0 + sb * (kSbBytes + 4), cap_u);
+      flush2(hi, lo, a0, a1);
+    }
+    {
+      const int step = plus_side ? kSbK : -kSbK;
+      int pe = plus_side ? j + kt0 + sb * kSbK : j - kt0 - sb * kSbK - 31;
+      uint32_t bsw = bsw0 + sb * (kSbBytes + 4);
+      for (; sb + 1 < n_edge; sb += 2) {
+        sb_edge(a0, a1, bits, pe, plus_side, M, bsw);
+        sb_edge(a0, a1, bits, pe + step, plus_side, M, bsw + (kSbBytes + 4));
+        flush2(hi, lo, a0, a1);
+        pe += 2 * step, bsw += 2 * (kSbBytes + 4);
+      }
+      if (sb < n_edge) {
+        sb_edge(a0, a1, bits, pe, plus_side, M, bsw);
+        flush2(hi, lo, a0, a1);
+        sb++;
+      }
+    }
+    for (; sb < n_all; sb++) {
+      sb_generic(a0, a1, bits, T, j, kt0 + sb * kSbK, kin, kout, plus_side, M, bsw0 + sb * (kSbBytes + 4), cap_u);
+      flush2(hi, lo, a0, a1);
+    }
   }
   if (!live) return;
   W.score[i - 1] = hi + lo;
