@@ -495,8 +495,40 @@ __global__ void __launch_bounds__(256) k_apply(WalkDev *hdr, const uint32_t *act
 constexpr int kSbFloats = 576;           // 6 groups x 3 tables x 32 entries
 constexpr int kSbBytes = kSbFloats * 4;  // 2304 bytes = 18 x 128
 
-// tables (rounded up to a 128-byte boundary inside the allocation) + one int
-size_t hot_batched_smem(uint32_t tile_sb) { return (size_t)tile_sb * kSbBytes + 256; }
+// tables (rounded up to a 128-byte boundary inside the allocation), two TMA staging
+// buffers of the tile's per-k values, and two ints
+size_t hot_batched_smem(uint32_t tile_sb) { return (size_t)tile_sb * kSbBytes + 2 * (size_t)tile_sb * kSbK * 16 + 256; }
+
+// ---- TMA bulk copies and mbarriers (sm_90 and later) ----
+__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16) signalling mbar
+__device__ __forceinline__ void tma_load_1d(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(mbar)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}"
+      : "=r"(done)
+      : "r"(mbar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// bounded wait: false if the phase did not complete within the iteration limit
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
+  for (int it = 0; it < (1 << 20); it++)
+    if (mbar_try_wait(mbar, parity)) return true;
+  return false;
+}
 
 template <int OFF>
 __device__ __forceinline__ float lds_at(uint32_t addr) {
@@ -520,13 +552,14 @@ __device__ __forceinline__ uint32_t window32_ro(const uint32_t *__restrict__ bit
 }
 
 // tables of group q of super-block sb of the tile (first k of the group: kg)
-__device__ __forceinline__ void build_group(float *tab, int sb, int q, const float4 *__restrict__ T, int kg, int L) {
+// (the tile's per-k values come from the shared staging buffer Ts, entry kg - kt0)
+__device__ __forceinline__ void build_group(float *tab, int sb, int q, const float4 *Ts, int kt0, int kg, int L) {
   float tp4[5], tm4[5], tp2[5], tm2[5];
 #pragma unroll
   for (int t = 0; t < 5; t++) {
     const int k = kg + t;
     float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (k < L) v = __ldg(T + k);
+    if (k < L) v = Ts[k - kt0];
     tp4[t] = v.x;
     tm4[t] = v.y;
     tp2[t] = v.z;
@@ -668,13 +701,19 @@ __device__ __forceinline__ int sb_count(int bound, int kt0, int off, int nsb) {
 }
 
 template <int NT, int NSB>
-__global__ void __launch_bounds__(NT) k_hot_batched(WalkDev *hdr, const HotItem *items) {
+__global__ void __launch_bounds__(NT, 1024 / NT) k_hot_batched(WalkDev *hdr, const HotItem *items) {
   static_assert(NSB <= 32, "the per-super-block swizzle assumes at most 32 super-blocks per tile");
   extern __shared__ __align__(128) float smem_raw[];
+  __shared__ __align__(8) uint64_t s_mbar[2];
   const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(smem_raw);
   const uint32_t tab_s = (raw_s + 127u) & ~127u;  // lookups OR a swizzle into the low 7 bits
   float *tab = smem_raw + (tab_s - raw_s) / 4;
-  int *s_kmax = reinterpret_cast<int *>(tab + NSB * kSbFloats);
+  constexpr int kTileK = NSB * kSbK;
+  float4 *stage = reinterpret_cast<float4 *>(tab + NSB * kSbFloats);  // 2 x kTileK staged T values
+  const uint32_t stage_s = tab_s + NSB * kSbBytes;
+  int *s_kmax = reinterpret_cast<int *>(stage + 2 * kTileK);
+  int *s_timeout = s_kmax + 1;
+  const uint32_t mbar_s = (uint32_t)__cvta_generic_to_shared(s_mbar);
   const HotItem it = items[blockIdx.x];
   WalkDev &W = hdr[it.slot];
   if (W.status != kRunning) return;
@@ -695,18 +734,41 @@ __global__ void __launch_bounds__(NT) k_hot_batched(WalkDev *hdr, const HotItem 
   const int w_kin_hi = __reduce_max_sync(0xffffffffu, kin);
   const int w_kout_lo = __reduce_min_sync(0xffffffffu, kout);
   const int w_kout_hi = warp_live ? __reduce_max_sync(0xffffffffu, kout) : 0;
-  if (threadIdx.x == 0) *s_kmax = 0;
+  if (threadIdx.x == 0) {
+    *s_kmax = 0;
+    *s_timeout = 0;
+    mbar_init(mbar_s, 1);
+    mbar_init(mbar_s + 8, 1);
+    fence_mbar_init();
+  }
   __syncthreads();
   if ((threadIdx.x & 31) == 0) atomicMax(s_kmax, w_kout_hi);
   __syncthreads();
   const int kmax = *s_kmax;
+  const int ntiles = (kmax + kTileK - 1) / kTileK;
+  // TMA bulk copy of tile t's per-k values T[kt0 .. kt0 + kTileK) (those below L) into buffer t & 1
+  auto stage_tile = [&](int t) {
+    const int kt0 = 1 + t * kTileK;
+    const uint32_t bytes = 16u * (uint32_t)min(kTileK, L - kt0);
+    const uint32_t mb = mbar_s + 8u * (t & 1);
+    fence_proxy_async();
+    mbar_expect_tx(mb, bytes);
+    tma_load_1d(stage_s + (uint32_t)((t & 1) * kTileK * 16), T + kt0, bytes, mb);
+  };
+  if (threadIdx.x == 0 && ntiles > 0) stage_tile(0);
 
   float hi = 0.f, lo = 0.f, a0 = 0.f, a1 = 0.f;
-  for (int kt0 = 1; kt0 <= kmax; kt0 += NSB * kSbK) {
-    __syncthreads();  // previous tile fully consumed
-    for (int t = threadIdx.x; t < 6 * NSB; t += NT) {
-      const int sb = t % NSB, q = t / NSB;
-      build_group(tab, sb, q, T, kt0 + sb * kSbK + 5 * q, L);
+  for (int tile = 0; tile < ntiles; tile++) {
+    const int kt0 = 1 + tile * kTileK;
+    __syncthreads();  // previous tile fully consumed (tables, and the staging buffer reused below)
+    if (threadIdx.x == 0 && tile + 1 < ntiles) stage_tile(tile + 1);
+    if ((int)threadIdx.x < 6 * NSB) {
+      if (!mbar_wait_bounded(mbar_s + 8u * (tile & 1), (uint32_t)(tile >> 1) & 1u)) *s_timeout = 1;
+      const float4 *Ts = stage + (tile & 1) * kTileK;
+      for (int t = threadIdx.x; t < 6 * NSB; t += NT) {
+        const int sb = t % NSB, q = t / NSB;
+        build_group(tab, sb, q, Ts, kt0, kt0 + sb * kSbK + 5 * q, L);
+      }
     }
     __syncthreads();
     // warp-uniform phases of this tile, in increasing k:
@@ -759,6 +821,17 @@ __global__ void __launch_bounds__(NT) k_hot_batched(WalkDev *hdr, const HotItem 
       sb_generic(a0, a1, bits, T, j, kt0 + sb * kSbK, kin, kout, plus_side, M, bsw0 + sb * (kSbBytes + 4), cap_u);
       flush2(hi, lo, a0, a1);
     }
+  }
+  if (*s_timeout) {
+    // a staged copy never arrived: give every copy of this block one more bounded wait,
+    // then mark the walk failed instead of using its scores
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int t = max(0, ntiles - 2); t < ntiles; t++) mbar_wait_bounded(mbar_s + 8u * (t & 1), (uint32_t)(t >> 1) & 1u);
+      W.error = (uint32_t)-5;  // PSL_ETIMEOUT of the library header
+      W.status = kError;
+    }
+    return;
   }
   if (!live) return;
   W.score[i - 1] = hi + lo;
