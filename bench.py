@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--serving", type=int, default=24, help="requests of the serving trace to run (0: skip)")
+    ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--hot-threads", type=int, default=0, help="force the neighbourhood-kernel block size")
     ap.add_argument("--hot-tile", type=int, default=0, help="force the k-tile (super-blocks of 30)")
     return ap.parse_args()
@@ -199,6 +201,25 @@ def stored_traffic(kernel: str, workload: str):
     return None
 
 
+def rank_specs(walks: int, rank: int):
+    """The walks one rank runs: the L=131071 workload with seeds offset by rank, so ranks never
+    share a walk (weak scaling: every rank keeps the same number of walks)."""
+    wl = W.batch_131071(walks=walks)
+    return wl, [W.WalkSpec(L=s.L, seed=s.seed + rank * walks, alpha1=s.alpha1, alpha2=s.alpha2, budget=s.budget)
+                for s in wl.walks]
+
+
+def aggregate(local_ms: float, local_units: int, world: int, dist=None, device=None):
+    """Whole-job throughput: units summed over ranks / the slowest rank's time."""
+    import torch
+    t = torch.tensor([local_ms], dtype=torch.float64, device=device)
+    u = torch.tensor([local_units], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / (float(t.item()) / 1000.0), float(t.item())
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -214,9 +235,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    wl = W.batch_131071(walks=args.walks)
-    specs = [W.WalkSpec(L=s.L, seed=s.seed + rank * args.walks, alpha1=s.alpha1, alpha2=s.alpha2, budget=s.budget)
-             for s in wl.walks]
+    wl, specs = rank_specs(args.walks, rank)
     L, N = specs[0].L, specs[0].N
     assert args.warmup + args.steps <= specs[0].budget and args.warmup >= 1
     need = sum(P.psl_walk_bytes(s.L, s.n_lmt, 0) for s in specs)
@@ -253,12 +272,8 @@ def run_ours(args):
         ms = e0.elapsed_time(e1)
         st = [ctx.poll(i) for i in ids[:4]]
         assert all(s["moves"] == args.warmup + args.steps for s in st)
-    t = torch.tensor([ms], device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
     flip_evals_rank = len(specs) * N * args.steps
-    value = world * flip_evals_rank / (ms_max / 1000.0)
+    value, ms_max = aggregate(ms, flip_evals_rank, world, dist, dev)
 
     # roofline of the dominant kernel (the neighbourhood score), live durations
     n_hot, hot_ms = prof.get("hot", (0, 0.0))
@@ -310,6 +325,19 @@ def run_ours(args):
                "d2h_bytes_per_step": (len(specs) * hdr_bytes * args.steps + len(specs) * L) / args.steps,
                "includes": "submit, walk initialisation, steps, status and best-sequence readback"}
 
+    # serving: Poisson arrivals of walks with L = 2^m - 1, m uniform in 10..20, continuous batching
+    serving = None
+    if args.serving > 0 and rank == 0:
+        from paper_2107_09801_gb300.serving import serve
+        trace = W.serving_trace(n_requests=args.serving, rate_hz=args.serving_rate)
+        arena_s = min(24 << 30, int(sum(P.psl_walk_bytes(r.spec.L, r.spec.n_lmt, 0) for r in trace) * 1.05) + (64 << 20))
+        with P.Context(arena_bytes=arena_s, stream=stream, max_walks=max(64, args.serving), device=local,
+                       **({"hot_threads": tuned[0], "hot_tile_sb": tuned[1]} if tuned else {})) as sc:
+            res = serve(sc, trace, steps_per_round=8)
+        serving = dict(res.summary(), rate_hz=args.serving_rate, trace="Poisson arrivals, m~U{10..20}, budgets "
+                       "~U{100..10^4}, alpha1~U{2..6}, alpha2~U{alpha1+4..13}, request r has seed r",
+                       arena_gb=arena_s / 1e9)
+
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -329,6 +357,7 @@ def run_ours(args):
                 "plain": plain,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
                 "paper_context": {"A100_one_walk_flip_evals_per_s_L131071": PAPER_A100_L131071},
+                "serving": serving,
                 "e2e": e2e}
         if not args.no_cpu_baseline:
             sampler = OracleSampler(L, N, 4)

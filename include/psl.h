@@ -237,6 +237,13 @@ PSL_API int psl_set_hot_config(psl_ctx *ctx, int32_t threads, int32_t tile_sb);
  * different streams with no ordering between them, race and give wrong results. */
 PSL_API int psl_autocorr_static(const int8_t *seq_dev, uint32_t L, int32_t *C_dev, void *stream);
 
+/* Test hook for the failure path (no counterpart in the paper): the walk's next
+ * neighbourhood pass waits for staged copies that are never issued, with a short limit,
+ * so its bounded waits run out; the walk then ends in PSL_ERROR with error PSL_ETIMEOUT
+ * while every other walk and the context carry on.  Nothing faults and nothing is left in
+ * flight.  PSL_ENOENT / PSL_EBUSY if the walk is unknown or not yet admitted. */
+PSL_API int psl_inject_stall(psl_ctx *ctx, int64_t id);
+
 /* Destroys the context and frees its device memory.  NULL is ignored. */
 PSL_API void psl_shutdown(psl_ctx *ctx);
 

@@ -65,7 +65,7 @@ assert TRACE_DTYPE.itemsize == 128  # psl_trace_rec has no implicit padding
 EXPORTED = ["psl_config_default", "psl_init", "psl_submit", "psl_submit_ex", "psl_step", "psl_poll", "psl_best",
             "psl_release", "psl_export_state", "psl_trace", "psl_autocorr", "psl_walk_bytes", "psl_shutdown",
             "psl_last_error", "psl_profile", "psl_profile_read", "psl_autotune", "psl_set_hot_config",
-            "psl_autocorr_static"]
+            "psl_autocorr_static", "psl_inject_stall"]
 
 _lib = None
 
@@ -103,6 +103,7 @@ def lib():
             "psl_autotune": (ct.c_int, [P, ct.c_int]),
             "psl_set_hot_config": (ct.c_int, [P, ct.c_int32, ct.c_int32]),
             "psl_autocorr_static": (ct.c_int, [P, ct.c_uint32, P, P]),
+            "psl_inject_stall": (ct.c_int, [P, ct.c_int64]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -341,6 +342,10 @@ class Context:
 
     def _set_hot(self, threads: int, tile_sb: int) -> None:
         psl_set_hot_config(self.h, threads, tile_sb)
+
+    def inject_stall(self, wid: int) -> None:
+        """Test hook: the walk's next neighbourhood pass runs out its bounded waits."""
+        _check(self.h, lib().psl_inject_stall(self.h, wid))
 
     def profile(self, enable: bool = True) -> None:
         psl_profile(self.h, enable)

@@ -22,6 +22,8 @@ constexpr int kSbK = 30;           // k per super-block (6 groups of 5)
 constexpr int kGroupK = 5;         // k per table group (32-entry tables)
 constexpr int kApplyPartStride = 32;  // u32 per apply-chunk partial record
 constexpr int kFlushBlockAdds = 64;   // FP32 additions per lane before a compensated flush
+constexpr int kKsplitMax = 16;        // most k-chunks one neighbour's score may be split into
+constexpr int kKchunkSbUnit = 32;     // k-chunks are whole multiples of 32 super-blocks (960 k)
 
 enum WalkStatus : uint32_t { kFree = 0, kRunning = 1, kDone = 2, kError = 3 };
 enum ApplyMode : uint32_t { kModeInit = 0, kModeMove = 1, kModeSwitch = 2 };
@@ -52,6 +54,7 @@ struct WalkDev {
   int32_t *C, *C_local;
   float4 *T;          // per k: (Tp4, Tm4, Tp2, Tm2), scaled by 2^(-alpha*e)
   float *score;       // FP32 filter score of window position i at [i-1]
+  float *score_part;  // per-k-chunk partial scores [chunk][N] when the k range is split
   int32_t *pslj;      // exact neighbour PSL (or INT32_MAX when not needed)
   int2 *ktau;         // near-peak list (k, C_k)
   uint32_t *cand;     // candidate window positions, ascending
@@ -75,6 +78,8 @@ struct WalkDev {
   uint32_t win_psl_i;
   uint32_t arrive;
   uint32_t alpha_next;
+  uint32_t ksplit, kchunk_sb;  // k-chunks of the neighbourhood kernel and their size (super-blocks)
+  uint32_t inject_stall;       // test hook: the next neighbourhood pass waits on copies never issued
   float score_min, bound;
   uint32_t flips[kMaxFlips];
   uint32_t F[kWideLimbs], value_local[kWideLimbs], value_step[kWideLimbs];
@@ -84,6 +89,8 @@ struct WalkDev {
 struct HotItem {
   uint32_t slot;
   uint32_t i0;  // first window position (1-based) of the block
+  uint32_t kc;  // k-chunk of the block (0 when the walk's k range is not split)
+  uint32_t pad;
 };
 
 struct LaunchCtx {
@@ -115,10 +122,12 @@ bool hot_config_supported(uint32_t threads, uint32_t tile_sb);  // block sizes 1
 // Candidate threshold shared bit-for-bit by the device select and the host select
 // of the plain form.  Returns the largest FP32 score that may still belong to the
 // exact argmin: min + 2B rounded up, with B bounding |FP32 score - exact score|.
-__host__ __device__ inline double score_bound(float S_abs, uint32_t alpha, uint32_t L) {
+// With the k range split into ksplit chunks, each chunk's partial score is rounded once
+// more and the partials are summed in chunk order (ksplit - 1 further roundings).
+__host__ __device__ inline double score_bound(float S_abs, uint32_t alpha, uint32_t L, uint32_t ksplit) {
   const double u = 5.9604644775390625e-08;  // 2^-24
-  const double nflush = (double)(L / kSbK + 2);
-  const double rel = (2.0 * alpha + 68.0) * u + (nflush * u) * (nflush * u);
+  const double nflush = (double)(L / kSbK + 2 * ksplit);
+  const double rel = (2.0 * alpha + 68.0 + 2.0 * ksplit) * u + (nflush * u) * (nflush * u);
   return rel * (double)S_abs * 1.01 + (double)L * 7.52316384526264e-37;  // + L * 2^-120
 }
 

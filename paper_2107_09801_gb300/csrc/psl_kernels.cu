@@ -524,8 +524,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
   return done != 0;
 }
 // bounded wait: false if the phase did not complete within the iteration limit
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
-  for (int it = 0; it < (1 << 20); it++)
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, int limit = 1 << 20) {
+  for (int it = 0; it < limit; it++)
     if (mbar_try_wait(mbar, parity)) return true;
   return false;
 }
@@ -745,25 +745,34 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_hot_batched(WalkDev *hdr, con
   if ((threadIdx.x & 31) == 0) atomicMax(s_kmax, w_kout_hi);
   __syncthreads();
   const int kmax = *s_kmax;
-  const int ntiles = (kmax + kTileK - 1) / kTileK;
+  // tiles of this block: all of them, or those of its k-chunk when the k range is split
+  const int tiles_per_chunk = (int)W.kchunk_sb / NSB;
+  const int tile_lo = W.ksplit > 1 ? (int)it.kc * tiles_per_chunk : 0;
+  const int tile_hi = W.ksplit > 1 ? min((kmax + kTileK - 1) / kTileK, tile_lo + tiles_per_chunk)
+                                   : (kmax + kTileK - 1) / kTileK;
+  const int ntiles = max(0, tile_hi - tile_lo);
   // TMA bulk copy of tile t's per-k values T[kt0 .. kt0 + kTileK) (those below L) into buffer t & 1
   auto stage_tile = [&](int t) {
-    const int kt0 = 1 + t * kTileK;
+    const int kt0 = 1 + (tile_lo + t) * kTileK;
     const uint32_t bytes = 16u * (uint32_t)min(kTileK, L - kt0);
     const uint32_t mb = mbar_s + 8u * (t & 1);
     fence_proxy_async();
     mbar_expect_tx(mb, bytes);
     tma_load_1d(stage_s + (uint32_t)((t & 1) * kTileK * 16), T + kt0, bytes, mb);
   };
-  if (threadIdx.x == 0 && ntiles > 0) stage_tile(0);
+  // test hook: no copy is issued, so every wait below runs out (short limit) and the walk
+  // is marked failed; nothing is left in flight
+  const bool stall = W.inject_stall != 0;
+  const int wait_limit = stall ? 64 : (1 << 20);
+  if (threadIdx.x == 0 && ntiles > 0 && !stall) stage_tile(0);
 
   float hi = 0.f, lo = 0.f, a0 = 0.f, a1 = 0.f;
   for (int tile = 0; tile < ntiles; tile++) {
-    const int kt0 = 1 + tile * kTileK;
+    const int kt0 = 1 + (tile_lo + tile) * kTileK;
     __syncthreads();  // previous tile fully consumed (tables, and the staging buffer reused below)
-    if (threadIdx.x == 0 && tile + 1 < ntiles) stage_tile(tile + 1);
+    if (threadIdx.x == 0 && tile + 1 < ntiles && !stall) stage_tile(tile + 1);
     if ((int)threadIdx.x < 6 * NSB) {
-      if (!mbar_wait_bounded(mbar_s + 8u * (tile & 1), (uint32_t)(tile >> 1) & 1u)) *s_timeout = 1;
+      if (!mbar_wait_bounded(mbar_s + 8u * (tile & 1), (uint32_t)(tile >> 1) & 1u, wait_limit)) *s_timeout = 1;
       const float4 *Ts = stage + (tile & 1) * kTileK;
       for (int t = threadIdx.x; t < 6 * NSB; t += NT) {
         const int sb = t % NSB, q = t / NSB;
@@ -827,14 +836,20 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_hot_batched(WalkDev *hdr, con
     // then mark the walk failed instead of using its scores
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int t = max(0, ntiles - 2); t < ntiles; t++) mbar_wait_bounded(mbar_s + 8u * (t & 1), (uint32_t)(t >> 1) & 1u);
+      if (!stall)
+        for (int t = max(0, ntiles - 2); t < ntiles; t++) mbar_wait_bounded(mbar_s + 8u * (t & 1), (uint32_t)(t >> 1) & 1u);
       W.error = (uint32_t)-5;  // PSL_ETIMEOUT of the library header
       W.status = kError;
     }
     return;
   }
   if (!live) return;
-  W.score[i - 1] = hi + lo;
+  if (W.ksplit > 1) {
+    W.score_part[(size_t)it.kc * N + (i - 1)] = hi + lo;
+    if (it.kc != 0) return;
+  } else {
+    W.score[i - 1] = hi + lo;
+  }
 
   // exact neighbour PSL, only when some neighbour may beat psl_best
   int pj = INT_MAX;
@@ -908,6 +923,16 @@ __global__ void __launch_bounds__(1024) k_select(WalkDev *hdr, const uint32_t *a
   const int N = (int)W.N;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
   const float *score = W.score;
+  const uint32_t ksplit = W.ksplit;
+  if (ksplit > 1) {
+    // partial scores of the k-chunks, summed in chunk order
+    for (int i = tid; i < N; i += blockDim.x) {
+      float sc = W.score_part[i];
+      for (uint32_t c = 1; c < ksplit; c++) sc += W.score_part[(size_t)c * N + i];
+      W.score[i] = sc;
+    }
+    __syncthreads();
+  }
 
   float m = FLT_MAX;
   for (int i = tid; i < N; i += blockDim.x) m = fminf(m, score[i]);
@@ -922,7 +947,7 @@ __global__ void __launch_bounds__(1024) k_select(WalkDev *hdr, const uint32_t *a
   }
   __syncthreads();
   m = s_m;
-  const double B = score_bound(W.S_abs, W.alpha, W.L);
+  const double B = score_bound(W.S_abs, W.alpha, W.L, ksplit);
   const float thr = __double2float_ru((double)m + 2.0 * B);
 
   // ordered compaction of {i : score <= thr}: each thread owns a contiguous segment

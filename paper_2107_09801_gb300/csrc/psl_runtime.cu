@@ -32,7 +32,7 @@ double now_s() {
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-  size_t bits, bits_local, bits_best, C, C_local, T, score, pslj, ktau, cand, rc_part, ap_part, trace, total;
+  size_t bits, bits_local, bits_best, C, C_local, T, score, score_part, pslj, ktau, cand, rc_part, ap_part, trace, total;
 };
 
 Layout layout_for(uint32_t L, uint32_t N, uint32_t trace_cap) {
@@ -54,6 +54,7 @@ Layout layout_for(uint32_t L, uint32_t N, uint32_t trace_cap) {
   o.C_local = take((size_t)L * 4);
   o.T = take((size_t)L * 16);
   o.score = take((size_t)N * 4);
+  o.score_part = take((size_t)kKsplitMax * N * 4);
   o.pslj = take((size_t)N * 4);
   o.ktau = take((size_t)L * 8);
   o.cand = take((size_t)N * 4);
@@ -138,6 +139,7 @@ struct psl_ctx {
   bool active_dirty = true;
   uint32_t nitems = 0, max_chunk_apply = 1, max_chunk_rc = 1;
   int64_t next_id = 0;
+  uint32_t sm_count = 152;
   std::string err;
   // CUDA graph of steps_per_graph steps over the current active set
   cudaGraphExec_t graph = nullptr;
@@ -304,6 +306,11 @@ extern "C" int psl_init(const psl_config *cfg_in, psl_ctx **out) {
     }
     ctx->own_arena = true;
   }
+  {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg.device) == cudaSuccess && sms > 0)
+      ctx->sm_count = (uint32_t)sms;
+  }
   if (prepare_kernels() != cudaSuccess) {
     cudaGetLastError();
     fail(nullptr, PSL_ECUDA, "kernel attribute setup failed");
@@ -424,6 +431,9 @@ static void fill_header(psl_ctx *ctx, HostWalk &w, WalkDev &h) {
   h.C_local = (int32_t *)(base + w.lay.C_local);
   h.T = (float4 *)(base + w.lay.T);
   h.score = (float *)(base + w.lay.score);
+  h.score_part = (float *)(base + w.lay.score_part);
+  h.ksplit = 1;
+  h.kchunk_sb = kKchunkSbUnit;
   h.pslj = (int32_t *)(base + w.lay.pslj);
   h.ktau = (int2 *)(base + w.lay.ktau);
   h.cand = (uint32_t *)(base + w.lay.cand);
@@ -446,9 +456,26 @@ static int rebuild_active(psl_ctx *ctx) {
   std::vector<HotItem> items;
   ctx->max_chunk_apply = 1;
   ctx->max_chunk_rc = 1;
+  // Split every walk's k range into chunks when the neighbour blocks alone would leave
+  // SMs idle (few walks, or a long walk on its own): aim for about four blocks per SM.
+  const uint32_t T_ = (uint32_t)ctx->cfg.hot_threads;
+  uint64_t nblocks = 0;
+  for (uint32_t s : ctx->active) nblocks += (ctx->h_hdr[s].N + T_ - 1) / T_;
+  const uint64_t target = 4ull * (uint64_t)ctx->sm_count;
+  uint32_t want = nblocks == 0 ? 1u : (uint32_t)std::min<uint64_t>(kKsplitMax, (target + nblocks - 1) / nblocks);
+  if (ctx->cfg.form == PSL_FORM_PLAIN) want = 1;  // the plain kernel scores each neighbour whole
   for (uint32_t s : ctx->active) {
-    const WalkDev &h = ctx->h_hdr[s];
-    for (uint32_t i0 = 1; i0 <= h.N; i0 += (uint32_t)ctx->cfg.hot_threads) items.push_back(HotItem{s, i0});
+    WalkDev &h = ctx->h_hdr[s];
+    const uint32_t unitK = kKchunkSbUnit * kSbK;
+    const uint32_t max_split = std::max<uint32_t>(1u, (h.L - 1 + unitK - 1) / unitK);
+    const uint32_t ks = std::min(want, max_split);
+    const uint32_t units = ((h.L - 1 + unitK - 1) / unitK + ks - 1) / ks;  // chunk size in 960-k units
+    h.ksplit = ks;
+    h.kchunk_sb = units * kKchunkSbUnit;
+    CK(cudaMemcpyAsync((char *)(ctx->d_hdr + s) + offsetof(WalkDev, ksplit), &h.ksplit, 8, cudaMemcpyHostToDevice,
+                       ctx->stream));
+    for (uint32_t i0 = 1; i0 <= h.N; i0 += T_)
+      for (uint32_t c = 0; c < ks; c++) items.push_back(HotItem{s, i0, c, 0});
     ctx->max_chunk_apply = std::max(ctx->max_chunk_apply, h.nchunk_apply);
     ctx->max_chunk_rc = std::max(ctx->max_chunk_rc, h.nchunk_rc);
   }
@@ -632,7 +659,7 @@ static void host_select(const WalkDev &h, const std::vector<float> &score, const
   const uint32_t N = h.N;
   float m = 3.4028234663852886e38f;
   for (uint32_t i = 0; i < N; i++) m = std::min(m, score[i]);
-  const double B = score_bound(h.S_abs, h.alpha, h.L);
+  const double B = score_bound(h.S_abs, h.alpha, h.L, 1u);
   const double td = (double)m + 2.0 * B;
   float thr = (float)td;
   if ((double)thr < td) thr = std::nextafter(thr, 3.4e38f);  // round up
@@ -1002,5 +1029,17 @@ extern "C" int psl_set_hot_config(psl_ctx *ctx, int32_t threads, int32_t tile_sb
   ctx->cfg.hot_threads = threads;
   ctx->cfg.hot_tile_sb = tile_sb;
   ctx->active_dirty = true;  // the block list depends on the block size
+  return PSL_OK;
+}
+
+extern "C" int psl_inject_stall(psl_ctx *ctx, int64_t id) {
+  if (!ctx) return PSL_EINVAL;
+  HostWalk *w = find(ctx, id);
+  if (!w) return PSL_ENOENT;
+  if (w->slot < 0) return PSL_EBUSY;
+  const uint32_t one = 1;
+  CK(cudaMemcpyAsync((char *)(ctx->d_hdr + w->slot) + offsetof(WalkDev, inject_stall), &one, 4,
+                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
   return PSL_OK;
 }

@@ -1,0 +1,75 @@
+"""Serving loop: continuous batching of walk requests through the C ABI.
+
+Requests arrive over time (an arrival trace); every request is submitted as soon as it
+has arrived, the library admits it into the batch as soon as the device arena has room,
+every admitted walk advances together in the batched kernels, and finished walks are
+read out and released at once so their memory serves the next request.  Latency is the
+time from arrival to the moment the walk's result has been read back.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from .binding import PSL_DONE, PSL_ERROR, Context
+
+
+@dataclass
+class ServeResult:
+    latencies_s: list = field(default_factory=list)   # arrival -> result read back, per request
+    psl_best: dict = field(default_factory=dict)      # request index -> best PSL
+    flip_evals: int = 0
+    wall_s: float = 0.0
+    errors: int = 0
+    max_active: int = 0
+
+    def percentile(self, p: float) -> float:
+        return float(np.percentile(np.asarray(self.latencies_s), p)) if self.latencies_s else float("nan")
+
+    def summary(self) -> dict:
+        return {"requests": len(self.latencies_s), "p50_s": self.percentile(50), "p99_s": self.percentile(99),
+                "mean_s": float(np.mean(self.latencies_s)) if self.latencies_s else float("nan"),
+                "flip_evals_per_s": self.flip_evals / self.wall_s if self.wall_s else 0.0,
+                "wall_s": self.wall_s, "errors": self.errors, "max_active": self.max_active}
+
+
+def serve(ctx: Context, trace, steps_per_round: int = 8, keep_sequences: bool = False) -> ServeResult:
+    """Runs a list of requests (objects with .t_arrival in seconds from the start and .spec,
+    a WalkSpec-like object with L, seed, alpha1, alpha2, budget, n_lmt, ls_lmt, flip_lmt,
+    topk) through the context and returns per-request latencies."""
+    res = ServeResult()
+    order = sorted(range(len(trace)), key=lambda r: trace[r].t_arrival)
+    nxt = 0
+    live = {}  # walk id -> request index
+    t0 = time.perf_counter()
+    while nxt < len(order) or live:
+        now = time.perf_counter() - t0
+        while nxt < len(order) and trace[order[nxt]].t_arrival <= now:
+            r = order[nxt]
+            s = trace[r].spec
+            wid = ctx.submit_ex(s.L, s.seed, s.alpha1, s.alpha2, s.budget, n_lmt=s.n_lmt, ls_lmt=s.ls_lmt,
+                                flip_lmt=s.flip_lmt, topk=s.topk)
+            live[wid] = r
+            nxt += 1
+        if not live:
+            # idle until the next arrival
+            time.sleep(max(0.0, trace[order[nxt]].t_arrival - (time.perf_counter() - t0)))
+            continue
+        ctx.step(steps_per_round)
+        for wid in list(live):
+            st = ctx.poll(wid)
+            if st["state"] in (PSL_DONE, PSL_ERROR):
+                r = live.pop(wid)
+                if st["state"] == PSL_DONE:
+                    psl, seq = ctx.best(wid)
+                    res.psl_best[r] = (psl, seq) if keep_sequences else psl
+                    res.flip_evals += int(st["flip_evals"])
+                else:
+                    res.errors += 1
+                res.latencies_s.append(time.perf_counter() - t0 - trace[r].t_arrival)
+                ctx.release(wid)
+        res.max_active = max(res.max_active, len(live))
+    res.wall_s = time.perf_counter() - t0
+    return res

@@ -95,3 +95,13 @@ def parallel_eval(s, C, alpha, js, workers=None):
     vals = [v for r in res for v in r[0]]
     psls = np.concatenate([r[1] for r in res])
     return vals, psls
+
+
+DECISION_FIELDS = ("step", "start", "kstar", "alpha", "unimproved", "psl", "psl_best", "win_psl", "win_psl_j",
+                   "flags", "nflip", "value_step", "value_exact")
+
+
+def same_decisions(a, b) -> bool:
+    """Equality of two GPU traces on every decision field (FP32 filter scores, the bound
+    and the candidate count may differ between launch configurations)."""
+    return len(a) == len(b) and all(np.array_equal(a[f], b[f]) for f in DECISION_FIELDS)
