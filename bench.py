@@ -332,6 +332,7 @@ def run_ours(args):
         trace = W.serving_trace(n_requests=args.serving, rate_hz=args.serving_rate)
         arena_s = min(24 << 30, int(sum(P.psl_walk_bytes(r.spec.L, r.spec.n_lmt, 0) for r in trace) * 1.05) + (64 << 20))
         with P.Context(arena_bytes=arena_s, stream=stream, max_walks=max(64, args.serving), device=local,
+                       steps_per_graph=8,
                        **({"hot_threads": tuned[0], "hot_tile_sb": tuned[1]} if tuned else {})) as sc:
             res = serve(sc, trace, steps_per_round=8)
         serving = dict(res.summary(), rate_hz=args.serving_rate, trace="Poisson arrivals, m~U{10..20}, budgets "

@@ -93,22 +93,34 @@ struct HotItem {
   uint32_t pad;
 };
 
+// What one step's persistent kernels work on, kept in device memory so that a captured
+// CUDA graph of steps serves every batch composition: the host rewrites it between launches.
+struct Schedule {
+  uint32_t nactive;          // running walks listed in the active array
+  uint32_t nitems;           // neighbourhood work items
+  uint32_t max_chunk_apply;  // most update-pass chunks of any listed walk
+  uint32_t max_chunk_rc;     // most re-check chunks of any listed walk
+  uint32_t hot_next;         // next neighbourhood item to hand out (reset by k_decide)
+  uint32_t pad[3];
+};
+
 struct LaunchCtx {
-  WalkDev *hdr;          // device array of walk slots
+  WalkDev *hdr;            // device array of walk slots
   const uint32_t *active;  // device list of active slots
-  uint32_t nactive;
-  const HotItem *items;  // device list of neighbourhood blocks
-  uint32_t nitems;
-  uint32_t max_chunk_apply, max_chunk_rc;
-  uint32_t hot_threads;  // neighbours per block of the batched kernel
-  uint32_t hot_tile_sb;  // super-blocks per k-tile
+  Schedule *sched;         // device schedule of this launch sequence
+  const HotItem *items;    // device list of neighbourhood blocks
+  uint32_t hot_threads;    // neighbours per block of the batched kernel
+  uint32_t hot_tile_sb;    // super-blocks per k-tile
+  uint32_t sm_count;
+  uint32_t maxL;           // longest walk of an initialisation launch
+  uint32_t ninit;          // walks of an initialisation launch
   cudaStream_t stream;
 };
 
 // ---- launchers (psl_kernels.cu) ----
 cudaError_t prepare_kernels();  // one-off kernel attributes (call before any capture)
 cudaError_t launch_init_bits(const LaunchCtx &c);
-cudaError_t launch_autocorr(const LaunchCtx &c, uint32_t maxL);
+cudaError_t launch_autocorr(const LaunchCtx &c);
 cudaError_t launch_apply(const LaunchCtx &c);
 cudaError_t launch_hot_batched(const LaunchCtx &c);
 cudaError_t launch_hot_plain(WalkDev *hdr_one, uint32_t N, cudaStream_t s);

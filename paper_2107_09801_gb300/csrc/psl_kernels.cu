@@ -300,14 +300,12 @@ __global__ void k_start_init(WalkDev *hdr, const uint32_t *active, uint32_t nact
 // apply: the O(L) update pass (init / move / switch) fused with the next window's
 // tables, PSL, sum of |T| and the near-peak list; the last block to arrive finalises.
 // ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_apply(WalkDev *hdr, const uint32_t *active) {
+__device__ __forceinline__ void apply_one(WalkDev &W, uint32_t chunk) {
   __shared__ int s_max[8];
   __shared__ float s_sum[8];
   __shared__ uint32_t s_F[256 / 32][kWideLimbs];
   __shared__ uint32_t s_last;
-  WalkDev &W = hdr[active[blockIdx.y]];
   if (W.status != kRunning) return;
-  const uint32_t chunk = blockIdx.x;
   if (chunk >= W.nchunk_apply) return;
   const int L = (int)W.L;
   const int k0 = (int)chunk * kApplyChunk, k1 = min(k0 + kApplyChunk, L);
@@ -471,6 +469,15 @@ __global__ void __launch_bounds__(256) k_apply(WalkDev *hdr, const uint32_t *act
       W.start = (uint32_t)(splitmix64(W.seed, W.rng_ctr++) % (uint64_t)W.L);
     }
     W.arrive = 0;
+  }
+}
+
+// persistent grid over (walk, chunk) pairs of the schedule
+__global__ void __launch_bounds__(256) k_apply(WalkDev *hdr, const uint32_t *active, const Schedule *sched) {
+  const uint32_t nch = sched->max_chunk_apply, V = sched->nactive * nch;
+  for (uint32_t v = blockIdx.x; v < V; v += gridDim.x) {
+    __syncthreads();  // shared reduction buffers of the previous pair are free
+    apply_one(hdr[active[v / nch]], v % nch);
   }
 }
 
@@ -700,8 +707,10 @@ __device__ __forceinline__ int sb_count(int bound, int kt0, int off, int nsb) {
   return d < 0 ? 0 : min(nsb, d / kSbK + 1);
 }
 
+// Scores one work item (a block of window positions, possibly one k-chunk of them).
+// Returns false when a staged copy timed out: the block must then stop taking work.
 template <int NT, int NSB>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_hot_batched(WalkDev *hdr, const HotItem *items) {
+__device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem it) {
   static_assert(NSB <= 32, "the per-super-block swizzle assumes at most 32 super-blocks per tile");
   extern __shared__ __align__(128) float smem_raw[];
   __shared__ __align__(8) uint64_t s_mbar[2];
@@ -714,9 +723,8 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_hot_batched(WalkDev *hdr, con
   int *s_kmax = reinterpret_cast<int *>(stage + 2 * kTileK);
   int *s_timeout = s_kmax + 1;
   const uint32_t mbar_s = (uint32_t)__cvta_generic_to_shared(s_mbar);
-  const HotItem it = items[blockIdx.x];
   WalkDev &W = hdr[it.slot];
-  if (W.status != kRunning) return;
+  if (W.status != kRunning) return true;
   const int L = (int)W.L, N = (int)W.N;
   const uint32_t *__restrict__ bits = W.bits;
   const float4 *__restrict__ T = W.T;
@@ -841,12 +849,12 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_hot_batched(WalkDev *hdr, con
       W.error = (uint32_t)-5;  // PSL_ETIMEOUT of the library header
       W.status = kError;
     }
-    return;
+    return stall;  // after a real timeout a copy may still be in flight: stop using this block
   }
-  if (!live) return;
+  if (!live) return true;
   if (W.ksplit > 1) {
     W.score_part[(size_t)it.kc * N + (i - 1)] = hi + lo;
-    if (it.kc != 0) return;
+    if (it.kc != 0) return true;
   } else {
     W.score[i - 1] = hi + lo;
   }
@@ -858,6 +866,22 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_hot_batched(WalkDev *hdr, con
     pj = neighbour_psl(W, W.ktau, (int)W.nktau, j, L, sj, W.psl - 8, 0);
   }
   W.pslj[i - 1] = pj;
+  return true;
+}
+
+// Persistent: every block takes work items one by one from the schedule's counter
+// (longest walks first in the item list).
+template <int NT, int NSB>
+__global__ void __launch_bounds__(NT, 1024 / NT) k_hot_batched(WalkDev *hdr, const HotItem *items, Schedule *sched) {
+  __shared__ uint32_t s_item;
+  for (;;) {
+    __syncthreads();  // the previous item's shared memory is free
+    if (threadIdx.x == 0) s_item = atomicAdd(&sched->hot_next, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= sched->nitems) break;
+    if (!hot_one<NT, NSB>(hdr, items[item])) break;
+  }
 }
 
 // ------------------------------------------------------------------------------------
@@ -910,7 +934,7 @@ __device__ __forceinline__ uint32_t float_order(float f) {
   return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
 }
 
-__global__ void __launch_bounds__(1024) k_select(WalkDev *hdr, const uint32_t *active) {
+__device__ __forceinline__ void select_one(WalkDev &W) {
   __shared__ float s_f[32];
   __shared__ unsigned long long s_u[32];
   __shared__ uint32_t s_cnt[32];
@@ -918,7 +942,6 @@ __global__ void __launch_bounds__(1024) k_select(WalkDev *hdr, const uint32_t *a
   __shared__ unsigned long long s_key;
   __shared__ uint32_t s_extra[16];
   __shared__ uint32_t s_total;
-  WalkDev &W = hdr[active[blockIdx.x]];
   if (W.status != kRunning) return;
   const int N = (int)W.N;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarps = blockDim.x >> 5;
@@ -1048,6 +1071,13 @@ __global__ void __launch_bounds__(1024) k_select(WalkDev *hdr, const uint32_t *a
   }
 }
 
+__global__ void __launch_bounds__(1024) k_select(WalkDev *hdr, const uint32_t *active, const Schedule *sched) {
+  for (uint32_t a = blockIdx.x; a < sched->nactive; a += gridDim.x) {
+    __syncthreads();
+    select_one(hdr[active[a]]);
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // recheck: exact Delta F = sum_{k: delta != 0} |C_k + delta|^alpha - |C_k|^alpha of the
 // candidates, one CTA per (chunk of k, candidate); positive and negative parts are
@@ -1070,15 +1100,13 @@ __device__ void recheck_body(const WalkDev &W, int j, int kbeg, int kend, uint32
   }
 }
 
-__global__ void __launch_bounds__(256) k_recheck(WalkDev *hdr, const uint32_t *active) {
+__device__ __forceinline__ void recheck_one(WalkDev &W, uint32_t chunk, uint32_t qslot) {
   __shared__ uint32_t s_w[8][2 * kWideLimbs];
-  WalkDev &W = hdr[active[blockIdx.z]];
   if (W.status != kRunning) return;
-  const uint32_t chunk = blockIdx.x;
   if (chunk >= W.nchunk_rc) return;
   const int L = (int)W.L;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (uint32_t q = blockIdx.y; q < W.ncand; q += kQcap) {
+  for (uint32_t q = qslot; q < W.ncand; q += kQcap) {
     const int i = (int)W.cand[q];
     const int j = (int)(((uint64_t)W.start + (uint64_t)i) % (uint64_t)L);
     const int kout = max(j, L - 1 - j);
@@ -1151,14 +1179,29 @@ __global__ void __launch_bounds__(256) k_recheck(WalkDev *hdr, const uint32_t *a
   }
 }
 
+// persistent grid over (walk, chunk) pairs of the schedule; each pair covers every
+// candidate of the walk (slots 0..kQcap-1 by chunk, later ones whole in chunk 0)
+__global__ void __launch_bounds__(256) k_recheck(WalkDev *hdr, const uint32_t *active, const Schedule *sched) {
+  const uint32_t nch = sched->max_chunk_rc, V = sched->nactive * nch;
+  for (uint32_t v = blockIdx.x; v < V; v += gridDim.x) {
+    WalkDev &W = hdr[active[v / nch]];
+    const uint32_t chunk = v % nch;
+    if (W.status != kRunning || chunk >= W.nchunk_rc) continue;  // uniform over the block
+    const uint32_t nslots = min(W.ncand, (uint32_t)kQcap);
+    for (uint32_t qslot = 0; qslot < nslots; qslot++) {
+      __syncthreads();
+      recheck_one(W, chunk, qslot);
+    }
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // decide: exact argmin over the candidates (strict "<" in scan order), the best-PSL
 // update, and the bookkeeping / phase switch of Alg. 1
 // ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_decide(WalkDev *hdr, const uint32_t *active) {
+__device__ __forceinline__ void decide_one(WalkDev &W) {
   __shared__ uint32_t s_best[kWideLimbs];
   __shared__ uint32_t s_bi;
-  WalkDev &W = hdr[active[blockIdx.x]];
   if (W.status != kRunning) return;
   const int L = (int)W.L;
   if (threadIdx.x == 0) {
@@ -1282,36 +1325,48 @@ __global__ void __launch_bounds__(256) k_decide(WalkDev *hdr, const uint32_t *ac
   }
 }
 
+__global__ void __launch_bounds__(256) k_decide(WalkDev *hdr, const uint32_t *active, Schedule *sched) {
+  // the neighbourhood kernel of this step has finished: rearm its work counter
+  if (blockIdx.x == 0 && threadIdx.x == 0) sched->hot_next = 0;
+  for (uint32_t a = blockIdx.x; a < sched->nactive; a += gridDim.x) {
+    __syncthreads();
+    decide_one(hdr[active[a]]);
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------
+static uint32_t g_hot_blocks_per_sm[3][2];  // occupancy of every variant, measured at set-up
+// resident blocks per SM of the other persistent kernels (one wave each)
+static uint32_t g_apply_per_sm = 4, g_select_per_sm = 1, g_recheck_per_sm = 3, g_decide_per_sm = 4;
+
 cudaError_t launch_init_bits(const LaunchCtx &c) {
-  uint32_t maxw = 0;
-  // the grid covers the largest walk; smaller ones return early
-  maxw = c.max_chunk_apply * (kApplyChunk / 32) + 2 * kGuardWords + 32;
-  dim3 grid((maxw + 255) / 256, c.nactive);
+  const uint32_t maxw = (c.maxL + 31) / 32 + 2 * kGuardWords;
+  dim3 grid((maxw + 255) / 256, c.ninit);
   k_init_bits<<<grid, 256, 0, c.stream>>>(c.hdr, c.active);
   return cudaGetLastError();
 }
 
-cudaError_t launch_autocorr(const LaunchCtx &c, uint32_t maxL) {
-  dim3 grid((maxL + 255) / 256, c.nactive);
+cudaError_t launch_autocorr(const LaunchCtx &c) {
+  dim3 grid((c.maxL + 255) / 256, c.ninit);
   k_autocorr<<<grid, 256, 0, c.stream>>>(c.hdr, c.active);
   return cudaGetLastError();
 }
 
 cudaError_t launch_start_init(const LaunchCtx &c) {
-  k_start_init<<<(c.nactive + 127) / 128, 128, 0, c.stream>>>(c.hdr, c.active, c.nactive);
+  k_start_init<<<(c.ninit + 127) / 128, 128, 0, c.stream>>>(c.hdr, c.active, c.ninit);
   return cudaGetLastError();
 }
 
 cudaError_t launch_apply(const LaunchCtx &c) {
-  dim3 grid(c.max_chunk_apply, c.nactive);
-  k_apply<<<grid, 256, 0, c.stream>>>(c.hdr, c.active);
+  k_apply<<<g_apply_per_sm * c.sm_count, 256, 0, c.stream>>>(c.hdr, c.active, c.sched);
   return cudaGetLastError();
 }
 
-using HotFn = void (*)(WalkDev *, const HotItem *);
+using HotFn = void (*)(WalkDev *, const HotItem *, Schedule *);
+
+static int variant_index(uint32_t threads) { return threads == 512 ? 2 : (threads == 128 ? 0 : 1); }
 
 static HotFn hot_variant(uint32_t threads, uint32_t tile_sb) {
   if (threads == 512) return tile_sb == 16 ? k_hot_batched<512, 16> : k_hot_batched<512, 32>;
@@ -1323,19 +1378,36 @@ bool hot_config_supported(uint32_t threads, uint32_t tile_sb) {
   return (threads == 128 || threads == 256 || threads == 512) && (tile_sb == 16 || tile_sb == 32);
 }
 
+static cudaError_t blocks_per_sm(const void *f, int threads, uint32_t *out) {
+  int nb = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, 0);
+  *out = (uint32_t)(nb > 0 ? nb : 1);
+  return e;
+}
+
 cudaError_t prepare_kernels() {
+  cudaError_t e0 = blocks_per_sm((const void *)k_apply, 256, &g_apply_per_sm);
+  if (e0 == cudaSuccess) e0 = blocks_per_sm((const void *)k_select, 1024, &g_select_per_sm);
+  if (e0 == cudaSuccess) e0 = blocks_per_sm((const void *)k_recheck, 256, &g_recheck_per_sm);
+  if (e0 == cudaSuccess) e0 = blocks_per_sm((const void *)k_decide, 256, &g_decide_per_sm);
+  if (e0 != cudaSuccess) return e0;
   for (uint32_t t : {128u, 256u, 512u})
     for (uint32_t sb : {16u, 32u}) {
-      cudaError_t e = cudaFuncSetAttribute(hot_variant(t, sb), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)hot_batched_smem(sb));
+      HotFn f = hot_variant(t, sb);
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hot_batched_smem(sb));
       if (e != cudaSuccess) return e;
+      int nb = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, (int)t, hot_batched_smem(sb));
+      if (e != cudaSuccess) return e;
+      g_hot_blocks_per_sm[variant_index(t)][sb == 32 ? 1 : 0] = (uint32_t)(nb > 0 ? nb : 1);
     }
   return cudaSuccess;
 }
 
 cudaError_t launch_hot_batched(const LaunchCtx &c) {
-  hot_variant(c.hot_threads, c.hot_tile_sb)<<<c.nitems, c.hot_threads, hot_batched_smem(c.hot_tile_sb), c.stream>>>(
-      c.hdr, c.items);
+  const uint32_t per_sm = g_hot_blocks_per_sm[variant_index(c.hot_threads)][c.hot_tile_sb == 32 ? 1 : 0];
+  hot_variant(c.hot_threads, c.hot_tile_sb)<<<per_sm * c.sm_count, c.hot_threads, hot_batched_smem(c.hot_tile_sb),
+                                              c.stream>>>(c.hdr, c.items, c.sched);
   return cudaGetLastError();
 }
 
@@ -1345,18 +1417,17 @@ cudaError_t launch_hot_plain(WalkDev *hdr_one, uint32_t N, cudaStream_t s) {
 }
 
 cudaError_t launch_select(const LaunchCtx &c) {
-  k_select<<<c.nactive, 1024, 0, c.stream>>>(c.hdr, c.active);
+  k_select<<<g_select_per_sm * c.sm_count, 1024, 0, c.stream>>>(c.hdr, c.active, c.sched);
   return cudaGetLastError();
 }
 
 cudaError_t launch_recheck(const LaunchCtx &c) {
-  dim3 grid(c.max_chunk_rc, kQcap, c.nactive);
-  k_recheck<<<grid, 256, 0, c.stream>>>(c.hdr, c.active);
+  k_recheck<<<g_recheck_per_sm * c.sm_count, 256, 0, c.stream>>>(c.hdr, c.active, c.sched);
   return cudaGetLastError();
 }
 
 cudaError_t launch_decide(const LaunchCtx &c) {
-  k_decide<<<c.nactive, 256, 0, c.stream>>>(c.hdr, c.active);
+  k_decide<<<g_decide_per_sm * c.sm_count, 256, 0, c.stream>>>(c.hdr, c.active, c.sched);
   return cudaGetLastError();
 }
 

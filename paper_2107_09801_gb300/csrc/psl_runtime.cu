@@ -129,6 +129,8 @@ struct psl_ctx {
   WalkDev *d_hdr = nullptr;
   std::vector<WalkDev> h_hdr;
   uint32_t *d_active = nullptr;
+  uint32_t *d_list_aux = nullptr;  // slot lists of initialisation and plain-form launches
+  Schedule *d_sched = nullptr;     // [0] batched steps, [1] initialisation, [2] plain form
   HotItem *d_items = nullptr;
   uint32_t items_cap = 0;
   uint32_t *h_pinned = nullptr;
@@ -320,12 +322,15 @@ extern "C" int psl_init(const psl_config *cfg_in, psl_ctx **out) {
   ctx->h_hdr.assign(cfg.max_walks, WalkDev{});
   if (cudaMalloc(&ctx->d_hdr, sizeof(WalkDev) * cfg.max_walks) != cudaSuccess ||
       cudaMalloc(&ctx->d_active, sizeof(uint32_t) * cfg.max_walks) != cudaSuccess ||
+      cudaMalloc(&ctx->d_list_aux, sizeof(uint32_t) * cfg.max_walks) != cudaSuccess ||
+      cudaMalloc(&ctx->d_sched, sizeof(Schedule) * 3) != cudaSuccess ||
       cudaMallocHost(&ctx->h_pinned, sizeof(uint32_t) * cfg.max_walks) != cudaSuccess) {
     cudaGetLastError();
     fail(nullptr, PSL_ENOMEM, "slot table allocation failed");
     return bail(PSL_ENOMEM);
   }
   cudaMemset(ctx->d_hdr, 0, sizeof(WalkDev) * cfg.max_walks);
+  cudaMemset(ctx->d_sched, 0, sizeof(Schedule) * 3);
   for (int s = cfg.max_walks - 1; s >= 0; s--) ctx->free_slots.push_back(s);
   *out = ctx;
   return PSL_OK;
@@ -342,6 +347,8 @@ extern "C" void psl_shutdown(psl_ctx *ctx) {
   if (ctx->own_arena && ctx->arena) cudaFree(ctx->arena);
   if (ctx->d_hdr) cudaFree(ctx->d_hdr);
   if (ctx->d_active) cudaFree(ctx->d_active);
+  if (ctx->d_list_aux) cudaFree(ctx->d_list_aux);
+  if (ctx->d_sched) cudaFree(ctx->d_sched);
   if (ctx->d_items) cudaFree(ctx->d_items);
   if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
   if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -480,9 +487,14 @@ static int rebuild_active(psl_ctx *ctx) {
     ctx->max_chunk_rc = std::max(ctx->max_chunk_rc, h.nchunk_rc);
   }
   if (items.size() > ctx->items_cap) {
+    CK(cudaStreamSynchronize(ctx->stream));
     if (ctx->d_items) cudaFree(ctx->d_items);
-    ctx->items_cap = (uint32_t)std::max<size_t>(items.size(), 1024);
+    ctx->items_cap = (uint32_t)std::max<size_t>(2 * items.size(), 4096);
     CK(cudaMalloc(&ctx->d_items, sizeof(HotItem) * ctx->items_cap));
+    if (ctx->graph) {  // the captured steps point at the old buffer
+      cudaGraphExecDestroy(ctx->graph);
+      ctx->graph = nullptr;
+    }
   }
   ctx->nitems = (uint32_t)items.size();
   if (!items.empty())
@@ -492,29 +504,40 @@ static int rebuild_active(psl_ctx *ctx) {
     std::copy(ctx->active.begin(), ctx->active.end(), ctx->h_pinned);
     CK(cudaMemcpyAsync(ctx->d_active, ctx->h_pinned, sizeof(uint32_t) * ctx->active.size(),
                        cudaMemcpyHostToDevice, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));  // h_pinned is reused
   }
-  if (ctx->graph) {
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
+  Schedule sc{};
+  sc.nactive = (uint32_t)ctx->active.size();
+  sc.nitems = ctx->nitems;
+  sc.max_chunk_apply = ctx->max_chunk_apply;
+  sc.max_chunk_rc = ctx->max_chunk_rc;
+  sc.hot_next = 0;
+  CK(cudaMemcpyAsync(ctx->d_sched, &sc, sizeof sc, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));  // h_pinned and sc are reused / temporaries
   ctx->active_dirty = false;
   return PSL_OK;
 }
 
-static LaunchCtx launch_ctx(psl_ctx *ctx, const uint32_t *d_list, uint32_t n) {
+static LaunchCtx launch_ctx(psl_ctx *ctx, const uint32_t *d_list, Schedule *d_sched) {
   LaunchCtx c{};
   c.hdr = ctx->d_hdr;
   c.active = d_list;
-  c.nactive = n;
+  c.sched = d_sched;
   c.items = ctx->d_items;
-  c.nitems = ctx->nitems;
-  c.max_chunk_apply = ctx->max_chunk_apply;
-  c.max_chunk_rc = ctx->max_chunk_rc;
   c.hot_threads = (uint32_t)ctx->cfg.hot_threads;
   c.hot_tile_sb = (uint32_t)ctx->cfg.hot_tile_sb;
+  c.sm_count = ctx->sm_count;
   c.stream = ctx->stream;
   return c;
+}
+
+static int upload_schedule(psl_ctx *ctx, Schedule *d, uint32_t nactive, uint32_t apply_chunks, uint32_t rc_chunks) {
+  Schedule sc{};
+  sc.nactive = nactive;
+  sc.max_chunk_apply = apply_chunks;
+  sc.max_chunk_rc = rc_chunks;
+  CK(cudaMemcpyAsync(d, &sc, sizeof sc, cudaMemcpyHostToDevice, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return PSL_OK;
 }
 
 static void pack_pm1(const int8_t *s, uint32_t L, std::vector<uint32_t> &words) {
@@ -555,20 +578,21 @@ static int admit(psl_ctx *ctx) {
     it = ctx->queue.erase(it);
   }
   if (fresh.empty()) return PSL_OK;
-  uint32_t *d_fresh = nullptr;
-  CK(cudaMalloc(&d_fresh, sizeof(uint32_t) * fresh.size()));
-  CK(cudaMemcpyAsync(d_fresh, fresh.data(), sizeof(uint32_t) * fresh.size(), cudaMemcpyHostToDevice, ctx->stream));
-  LaunchCtx c = launch_ctx(ctx, d_fresh, (uint32_t)fresh.size());
-  c.max_chunk_apply = maxchunk;
+  CK(cudaMemcpyAsync(ctx->d_list_aux, fresh.data(), sizeof(uint32_t) * fresh.size(), cudaMemcpyHostToDevice,
+                     ctx->stream));
+  int rc = upload_schedule(ctx, ctx->d_sched + 1, (uint32_t)fresh.size(), maxchunk, 1);
+  if (rc) return rc;
+  LaunchCtx c = launch_ctx(ctx, ctx->d_list_aux, ctx->d_sched + 1);
+  c.maxL = maxL;
+  c.ninit = (uint32_t)fresh.size();
   cudaError_t e = prof_begin(ctx, kPInit);
   if (e == cudaSuccess) e = launch_init_bits(c);
-  if (e == cudaSuccess) e = launch_autocorr(c, maxL);
+  if (e == cudaSuccess) e = launch_autocorr(c);
   if (e == cudaSuccess) e = launch_start_init(c);
   if (e == cudaSuccess) e = launch_apply(c);
   if (e == cudaSuccess) e = prof_end(ctx);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e == cudaSuccess) prof_collect(ctx);
-  cudaFree(d_fresh);
   if (e != cudaSuccess) return fail(ctx, PSL_ECUDA, "walk initialisation: %s", cudaGetErrorString(e));
   ctx->active_dirty = true;
   return PSL_OK;
@@ -619,7 +643,7 @@ static cudaError_t enqueue_batched_step(psl_ctx *ctx, const LaunchCtx &c, bool t
 
 static int run_batched(psl_ctx *ctx, uint32_t steps) {
   if (ctx->active.empty() || steps == 0) return PSL_OK;
-  LaunchCtx c = launch_ctx(ctx, ctx->d_active, (uint32_t)ctx->active.size());
+  LaunchCtx c = launch_ctx(ctx, ctx->d_active, ctx->d_sched);
   const uint32_t G = (uint32_t)ctx->cfg.steps_per_graph;
   uint32_t done = 0;
   if (G > 0) {
@@ -695,10 +719,10 @@ static int run_plain(psl_ctx *ctx, uint32_t steps) {
   for (uint32_t s : ctx->active) {
     WalkDev *dh = ctx->d_hdr + s;
     uint32_t list_host = s;
-    CK(cudaMemcpyAsync(ctx->d_active, &list_host, sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
-    LaunchCtx c = launch_ctx(ctx, ctx->d_active, 1);
-    c.max_chunk_apply = ctx->h_hdr[s].nchunk_apply;
-    c.max_chunk_rc = ctx->h_hdr[s].nchunk_rc;
+    CK(cudaMemcpyAsync(ctx->d_list_aux, &list_host, sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+    int rc = upload_schedule(ctx, ctx->d_sched + 2, 1, ctx->h_hdr[s].nchunk_apply, ctx->h_hdr[s].nchunk_rc);
+    if (rc) return rc;
+    LaunchCtx c = launch_ctx(ctx, ctx->d_list_aux, ctx->d_sched + 2);
     for (uint32_t t = 0; t < steps; t++) {
       WalkDev h;
       CK(cudaMemcpyAsync(&h, dh, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
@@ -972,11 +996,12 @@ extern "C" int psl_autocorr(psl_ctx *ctx, const int8_t *seq, uint32_t nseq, uint
     LaunchCtx c{};
     c.hdr = dh;
     c.active = dl;
-    c.nactive = nseq;
-    c.max_chunk_apply = (L + kApplyChunk - 1) / kApplyChunk;
+    c.maxL = L;
+    c.ninit = nseq;
+    c.sm_count = ctx->sm_count;
     c.stream = ctx->stream;
     e = launch_init_bits(c);
-    if (e == cudaSuccess) e = launch_autocorr(c, L);
+    if (e == cudaSuccess) e = launch_autocorr(c);
     if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   }
   for (uint32_t q = 0; q < nseq && e == cudaSuccess; q++)
@@ -1005,10 +1030,15 @@ extern "C" int psl_autotune(psl_ctx *ctx, int reps) {
       ctx->cfg.hot_threads = t;
       ctx->cfg.hot_tile_sb = sb;
       if ((rc = rebuild_active(ctx))) return rc;
-      LaunchCtx c = launch_ctx(ctx, ctx->d_active, (uint32_t)ctx->active.size());
+      LaunchCtx c = launch_ctx(ctx, ctx->d_active, ctx->d_sched);
+      uint32_t *next = &ctx->d_sched->hot_next;
       CK(launch_hot_batched(c));  // warm-up
+      CK(cudaMemsetAsync(next, 0, 4, ctx->stream));
       CK(cudaEventRecord(a, ctx->stream));
-      for (int r = 0; r < reps; r++) CK(launch_hot_batched(c));
+      for (int r = 0; r < reps; r++) {
+        CK(launch_hot_batched(c));
+        CK(cudaMemsetAsync(next, 0, 4, ctx->stream));  // the persistent kernel consumed its work counter
+      }
       CK(cudaEventRecord(b, ctx->stream));
       CK(cudaEventSynchronize(b));
       float ms = 0.f;
@@ -1019,6 +1049,10 @@ extern "C" int psl_autotune(psl_ctx *ctx, int reps) {
   cudaEventDestroy(b);
   ctx->cfg.hot_threads = best_t;
   ctx->cfg.hot_tile_sb = best_sb;
+  if (ctx->graph) {  // captured with another kernel variant
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
   if ((rc = rebuild_active(ctx))) return rc;
   return best_t | (best_sb << 16);
 }
@@ -1029,6 +1063,10 @@ extern "C" int psl_set_hot_config(psl_ctx *ctx, int32_t threads, int32_t tile_sb
   ctx->cfg.hot_threads = threads;
   ctx->cfg.hot_tile_sb = tile_sb;
   ctx->active_dirty = true;  // the block list depends on the block size
+  if (ctx->graph) {          // captured with another kernel variant
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
   return PSL_OK;
 }
 
