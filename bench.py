@@ -328,16 +328,15 @@ def run_ours(args):
     # serving: Poisson arrivals of walks with L = 2^m - 1, m uniform in 10..20, continuous batching
     serving = None
     if args.serving > 0 and rank == 0:
-        from paper_2107_09801_gb300.serving import serve
+        from paper_2107_09801_gb300.serving import serve_classes
         trace = W.serving_trace(n_requests=args.serving, rate_hz=args.serving_rate)
-        arena_s = min(24 << 30, int(sum(P.psl_walk_bytes(r.spec.L, r.spec.n_lmt, 0) for r in trace) * 1.05) + (64 << 20))
-        with P.Context(arena_bytes=arena_s, stream=stream, max_walks=max(64, args.serving), device=local,
-                       steps_per_graph=8,
-                       **({"hot_threads": tuned[0], "hot_tile_sb": tuned[1]} if tuned else {})) as sc:
-            res = serve(sc, trace, steps_per_round=8)
+        arena_s = min(24 << 30, int(sum(P.psl_walk_bytes(r.spec.L, r.spec.n_lmt, 0) for r in trace) * 1.5) + (256 << 20))
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        res = serve_classes(trace, arena_s, sm_count=sms, ctx_kwargs=dict(device=local))
         serving = dict(res.summary(), rate_hz=args.serving_rate, trace="Poisson arrivals, m~U{10..20}, budgets "
                        "~U{100..10^4}, alpha1~U{2..6}, alpha2~U{alpha1+4..13}, request r has seed r",
-                       arena_gb=arena_s / 1e9)
+                       arena_gb=arena_s / 1e9, classes="L<=2^14 on 12% of SMs, <=2^17 on 30%, <=2^20 on 58%; "
+                       "one stream and host thread each")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -87,6 +87,8 @@ typedef struct {
   int32_t hot_tile_sb;      /* k-tile of the batched kernel in super-blocks of 30 k: 16 or 32; 0 = auto */
   int32_t steps_per_graph;  /* steps captured per CUDA graph launch; 0 = plain launches */
   int32_t hot_threads;      /* neighbours per block of the batched kernel: 128, 256 or 512; 0 = auto */
+  int32_t max_sms;          /* SMs' worth of resident blocks the persistent kernels launch (0 = all);
+                               lets contexts on different streams share the GPU side by side */
 } psl_config;
 
 /* Per-walk parameters of psl_submit_ex.  n_lmt, flip_lmt <= 0 and ls_lmt < 0 take

@@ -26,7 +26,7 @@ class psl_config(ct.Structure):
     _fields_ = [("n_lmt", ct.c_int32), ("ls_lmt", ct.c_int32), ("flip_lmt", ct.c_int32), ("device", ct.c_int32),
                 ("arena_bytes", ct.c_uint64), ("arena", ct.c_void_p), ("stream", ct.c_void_p), ("form", ct.c_int32),
                 ("max_walks", ct.c_int32), ("hot_tile_sb", ct.c_int32), ("steps_per_graph", ct.c_int32),
-                ("hot_threads", ct.c_int32)]
+                ("hot_threads", ct.c_int32), ("max_sms", ct.c_int32)]
 
 
 class psl_walk_params(ct.Structure):
@@ -258,12 +258,13 @@ class Context:
 
     def __init__(self, *, form: str = "batched", arena_bytes: int = 0, arena_tensor=None, stream=None,
                  max_walks: int = 4096, n_lmt: int = 6912, ls_lmt: int = 2000, flip_lmt: int = 10, device: int = 0,
-                 hot_tile_sb: int = 0, steps_per_graph: int = 0, hot_threads: int = 0):
+                 hot_tile_sb: int = 0, steps_per_graph: int = 0, hot_threads: int = 0, max_sms: int = 0):
         cfg = psl_config_default()
         cfg.n_lmt, cfg.ls_lmt, cfg.flip_lmt, cfg.device = n_lmt, ls_lmt, flip_lmt, device
         cfg.form = PSL_FORM_PLAIN if form == "plain" else PSL_FORM_BATCHED
         cfg.max_walks, cfg.hot_tile_sb, cfg.steps_per_graph = max_walks, hot_tile_sb, steps_per_graph
         cfg.hot_threads = hot_threads
+        cfg.max_sms = max_sms
         self._arena_tensor = arena_tensor
         if arena_tensor is not None:
             cfg.arena = arena_tensor.data_ptr()

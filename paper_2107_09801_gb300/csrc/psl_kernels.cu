@@ -15,6 +15,7 @@
 #include <cfloat>
 #include <climits>
 #include <cstdint>
+#include <mutex>
 
 #include "psl_internal.h"
 
@@ -1385,7 +1386,7 @@ static cudaError_t blocks_per_sm(const void *f, int threads, uint32_t *out) {
   return e;
 }
 
-cudaError_t prepare_kernels() {
+static cudaError_t prepare_kernels_once() {
   cudaError_t e0 = blocks_per_sm((const void *)k_apply, 256, &g_apply_per_sm);
   if (e0 == cudaSuccess) e0 = blocks_per_sm((const void *)k_select, 1024, &g_select_per_sm);
   if (e0 == cudaSuccess) e0 = blocks_per_sm((const void *)k_recheck, 256, &g_recheck_per_sm);
@@ -1402,6 +1403,15 @@ cudaError_t prepare_kernels() {
       g_hot_blocks_per_sm[variant_index(t)][sb == 32 ? 1 : 0] = (uint32_t)(nb > 0 ? nb : 1);
     }
   return cudaSuccess;
+}
+
+// Kernel attributes are per device and process; contexts created on several host threads
+// share one set-up.
+cudaError_t prepare_kernels() {
+  static std::once_flag once;
+  static cudaError_t result = cudaSuccess;
+  std::call_once(once, [] { result = prepare_kernels_once(); });
+  return result;
 }
 
 cudaError_t launch_hot_batched(const LaunchCtx &c) {

@@ -260,7 +260,7 @@ extern "C" int psl_init(const psl_config *cfg_in, psl_ctx **out) {
   else
     psl_config_default(&cfg);
   if (cfg.n_lmt < 1 || cfg.ls_lmt < 0 || cfg.flip_lmt < 0 || cfg.flip_lmt > kMaxFlips || cfg.max_walks < 1 ||
-      (cfg.form != PSL_FORM_BATCHED && cfg.form != PSL_FORM_PLAIN) || cfg.steps_per_graph < 0 ||
+      (cfg.form != PSL_FORM_BATCHED && cfg.form != PSL_FORM_PLAIN) || cfg.steps_per_graph < 0 || cfg.max_sms < 0 ||
       !hot_config_supported(cfg.hot_threads ? (uint32_t)cfg.hot_threads : 256u,
                             cfg.hot_tile_sb ? (uint32_t)cfg.hot_tile_sb : 32u))
     return fail(nullptr, PSL_EINVAL, "invalid psl_config field");
@@ -312,6 +312,7 @@ extern "C" int psl_init(const psl_config *cfg_in, psl_ctx **out) {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg.device) == cudaSuccess && sms > 0)
       ctx->sm_count = (uint32_t)sms;
+    if (cfg.max_sms > 0) ctx->sm_count = std::min<uint32_t>(ctx->sm_count, (uint32_t)cfg.max_sms);
   }
   if (prepare_kernels() != cudaSuccess) {
     cudaGetLastError();

@@ -8,6 +8,7 @@ time from arrival to the moment the walk's result has been read back.
 """
 from __future__ import annotations
 
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -73,3 +74,54 @@ def serve(ctx: Context, trace, steps_per_round: int = 8, keep_sequences: bool = 
         res.max_active = max(res.max_active, len(live))
     res.wall_s = time.perf_counter() - t0
     return res
+
+
+# Length classes of serve_classes: (longest L of the class, share of the SMs, steps per round).
+# Short walks are bound by step latency, long ones by the neighbourhood kernel's throughput.
+DEFAULT_CLASSES = ((1 << 14, 0.12, 32), (1 << 17, 0.30, 16), (1 << 20, 0.58, 8))
+
+
+def serve_classes(trace, arena_bytes: int, sm_count: int = 152, classes=DEFAULT_CLASSES, ctx_kwargs=None,
+                  steps_per_graph: int = 8, keep_sequences: bool = False) -> ServeResult:
+    """Serves the trace with one context per length class, each on its own stream and host
+    thread, its persistent kernels launched for its share of the SMs, so that a short walk
+    no longer waits for the steps of long walks.  Requests are routed by L; arena bytes are
+    split between the classes in proportion to the bytes their requests need."""
+    from .binding import psl_walk_bytes
+    ctx_kwargs = dict(ctx_kwargs or {})
+    parts = [[] for _ in classes]
+    index = {id(req): r for r, req in enumerate(trace)}
+    for req in trace:
+        c = next(i for i, (lmax, _, _) in enumerate(classes) if req.spec.L <= lmax)
+        parts[c].append(req)
+    need = [sum(psl_walk_bytes(r.spec.L, r.spec.n_lmt, 0) for r in p) for p in parts]
+    results = [None] * len(classes)
+    errors = []
+
+    def run(ci):
+        try:
+            lmax, share, spr = classes[ci]
+            nbytes = max(64 << 20, int(arena_bytes * need[ci] / max(1, sum(need))))
+            with Context(arena_bytes=nbytes, max_walks=max(8, len(parts[ci])), max_sms=max(1, int(sm_count * share)),
+                         steps_per_graph=steps_per_graph, **ctx_kwargs) as ctx:
+                results[ci] = serve(ctx, parts[ci], steps_per_round=spr, keep_sequences=keep_sequences)
+        except Exception as e:  # surfaced to the caller below
+            errors.append(e)
+
+    t0 = time.perf_counter()
+    ths = [threading.Thread(target=run, args=(ci,)) for ci in range(len(classes)) if parts[ci]]
+    [t.start() for t in ths]
+    [t.join() for t in ths]
+    if errors:
+        raise errors[0]
+    out = ServeResult(wall_s=time.perf_counter() - t0)
+    for ci, r in enumerate(results):
+        if r is None:
+            continue
+        out.latencies_s += r.latencies_s
+        for local, v in r.psl_best.items():  # back to indices of the whole trace
+            out.psl_best[index[id(parts[ci][local])]] = v
+        out.flip_evals += r.flip_evals
+        out.errors += r.errors
+        out.max_active += r.max_active
+    return out

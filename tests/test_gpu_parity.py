@@ -319,3 +319,20 @@ def test_bounded_wait_timeout_marks_only_that_walk(P):
         ctx.run()
         assert ctx.poll(wid)["state"] == P.PSL_DONE
         compare_traces(ctx.trace(wid, extra.budget), oracle_walk(extra).run(extra.budget), "after timeout")
+
+
+# ------------------------------------------------------------------------------------------------
+# serving: requests arriving over time, served by length class on separate streams
+# ------------------------------------------------------------------------------------------------
+def test_serving_by_length_class_matches_oracle(P):
+    from paper_2107_09801_gb300.serving import serve_classes
+    trace = [W.Request(0.002 * r, W.WalkSpec(L=L, seed=500 + r, alpha1=2 + r % 4, alpha2=8 + r % 5,
+                                               budget=8 + 3 * (r % 5), ls_lmt=3, n_lmt=300))
+             for r, L in enumerate([127, 20000, 1023, 8191, 150000, 255, 40000, 4095, 511, 131071])]
+    res = serve_classes(trace, arena_bytes=2 << 30, keep_sequences=True)
+    assert res.errors == 0 and len(res.latencies_s) == len(trace)
+    for r, req in enumerate(trace):
+        w = oracle_walk(req.spec)
+        w.run(req.spec.budget)
+        psl, seq = res.psl_best[r]
+        assert psl == w.psl_best and np.array_equal(seq, w.sol_best), r
