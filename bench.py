@@ -52,6 +52,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--other-configs", type=int, default=1, help="also time the L=16383 x 4096 and L=1048575 x 148 batches")
     ap.add_argument("--serving", type=int, default=24, help="requests of the serving trace to run (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=200.0)
     ap.add_argument("--hot-threads", type=int, default=0, help="force the neighbourhood-kernel block size")
@@ -181,8 +182,9 @@ def run_reference(args):
 # our arm
 # ------------------------------------------------------------------------------------------------
 def kernel_source_hash() -> str:
+    """Hash of the sources of the neighbourhood kernel (its translation unit and headers)."""
     h = hashlib.sha256()
-    for fn in ("psl_kernels.cu", "psl_internal.h"):
+    for fn in ("psl_hot.cu", "psl_device.cuh", "psl_internal.h"):
         with open(os.path.join(ROOT, "paper_2107_09801_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -325,6 +327,38 @@ def run_ours(args):
                "d2h_bytes_per_step": (len(specs) * hdr_bytes * args.steps + len(specs) * L) / args.steps,
                "includes": "submit, walk initialisation, steps, status and best-sequence readback"}
 
+    # the other batch configurations of the survey: throughput only (a few timed steps each)
+    others = None
+    if args.other_configs and rank == 0:
+        others = {}
+        for wl_o in (W.batch_16383(), W.batch_1048575()):
+            specs_o = list(wl_o.walks)
+            need_o = sum(P.psl_walk_bytes(x.L, x.n_lmt, 0) for x in specs_o)
+            with P.Context(arena_bytes=int(need_o * 1.1) + (64 << 20), stream=stream, max_walks=len(specs_o),
+                           device=local) as oc:
+                for x in specs_o:
+                    oc.submit_ex(x.L, x.seed, x.alpha1, x.alpha2, x.budget, topk=x.topk)
+                torch.cuda.synchronize(dev)
+                t_init = time.perf_counter()
+                oc.step(1)
+                t_init = time.perf_counter() - t_init
+                tune_o = oc.autotune(reps=1)
+                oc.step(2)
+                oc.profile(True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                oc.step(5)
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                prof_o = oc.profile_read()
+                ms_o = e0.elapsed_time(e1)
+            Lo, No = specs_o[0].L, specs_o[0].N
+            n_hot, hot_ms_o = prof_o.get("hot", (0, 0.0))
+            others[wl_o.name] = {"value": len(specs_o) * No * 5 / (ms_o / 1000.0), "unit": UNIT,
+                                 "ms_per_step": ms_o / 5, "hot_kernel": {"threads": tune_o[0], "tile_superblocks": tune_o[1]},
+                                 "roofline_frac": (len(specs_o) * No * 2 * (Lo - 1)) / (hot_ms_o / max(n_hot, 1) / 1000.0) / peak,
+                                 "init_s": t_init, "description": wl_o.description}
+
     # serving: Poisson arrivals of walks with L = 2^m - 1, m uniform in 10..20, continuous batching
     serving = None
     if args.serving > 0 and rank == 0:
@@ -358,6 +392,7 @@ def run_ours(args):
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
                 "paper_context": {"A100_one_walk_flip_evals_per_s_L131071": PAPER_A100_L131071},
                 "serving": serving,
+                "other_configs": others,
                 "e2e": e2e}
         if not args.no_cpu_baseline:
             sampler = OracleSampler(L, N, 4)

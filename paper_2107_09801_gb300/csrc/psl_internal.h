@@ -118,7 +118,8 @@ struct LaunchCtx {
 };
 
 // ---- launchers (psl_kernels.cu) ----
-cudaError_t prepare_kernels();  // one-off kernel attributes (call before any capture)
+cudaError_t prepare_kernels();      // one-off kernel attributes (call before any capture)
+cudaError_t prepare_hot_kernels();  // the neighbourhood kernels' part of it (psl_hot.cu)
 cudaError_t launch_init_bits(const LaunchCtx &c);
 cudaError_t launch_autocorr(const LaunchCtx &c);
 cudaError_t launch_apply(const LaunchCtx &c);

@@ -5,233 +5,24 @@
 // One walk step (the body of the while loop of Algorithm 1) is five kernels:
 //   hot     FP32 filter score of every neighbour in the window (Eq. 4 through the
 //           one-element flip of Sec. 3) and, when it can matter, its exact PSL (Eq. 3)
+//           -- in psl_hot.cu
 //   select  minimum score, the certified candidate set {score <= min + 2B} plus the
 //           FP32 top-k, and the first neighbour of minimum PSL
 //   recheck exact 384-bit Delta F of every candidate
 //   decide  exact argmin (first in scan order), bookkeeping and phase switch of Alg. 1
 //   apply   O(L) update of C, PSL, the next step's per-k tables and near-peak list
-// Every wait between blocks is a "last block to arrive finishes the walk" counter:
-// no block ever spins.
+// This file holds the walk initialisation and the last four.  Work shared between blocks
+// of a walk ends in a "last block to arrive finishes the walk" counter: no block here
+// waits on another.
 #include <cfloat>
 #include <climits>
 #include <cstdint>
 #include <mutex>
 
+#include "psl_device.cuh"
 #include "psl_internal.h"
 
 namespace psl {
-
-// ------------------------------------------------------------------------------------
-// helpers
-// ------------------------------------------------------------------------------------
-// Rand of Alg. 1: SplitMix64 (Steele, Lea, Flood 2014), draw n of the walk seeded S.
-__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t n) {
-  uint64_t z = seed + (n + 1ull) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  return z ^ (z >> 31);
-}
-
-// 32 sequence bits starting at bit position pos (pos may lie in the guard words).
-__device__ __forceinline__ uint32_t window32(const uint32_t *bits, int pos) {
-  const int w = pos >> 5;  // floor division
-  return __funnelshift_r(bits[w], bits[w + 1], pos & 31);
-}
-
-__device__ __forceinline__ int getbit(const uint32_t *bits, int pos) { return (bits[pos >> 5] >> (pos & 31)) & 1; }
-
-// s_pos in {+1,-1}
-__device__ __forceinline__ int sval(const uint32_t *bits, int pos) { return 1 - 2 * getbit(bits, pos); }
-
-// ---- 384-bit unsigned arithmetic on 12 x 32-bit limbs (carry chains in PTX) ----
-__device__ __forceinline__ void wide_zero(uint32_t (&a)[kWideLimbs]) {
-#pragma unroll
-  for (int i = 0; i < kWideLimbs; i++) a[i] = 0;
-}
-
-__device__ __forceinline__ void wide_add(uint32_t (&a)[kWideLimbs], const uint32_t (&b)[kWideLimbs]) {
-  asm("add.cc.u32 %0, %0, %12;\n\t"
-      "addc.cc.u32 %1, %1, %13;\n\t"
-      "addc.cc.u32 %2, %2, %14;\n\t"
-      "addc.cc.u32 %3, %3, %15;\n\t"
-      "addc.cc.u32 %4, %4, %16;\n\t"
-      "addc.cc.u32 %5, %5, %17;\n\t"
-      "addc.cc.u32 %6, %6, %18;\n\t"
-      "addc.cc.u32 %7, %7, %19;\n\t"
-      "addc.cc.u32 %8, %8, %20;\n\t"
-      "addc.cc.u32 %9, %9, %21;\n\t"
-      "addc.cc.u32 %10, %10, %22;\n\t"
-      "addc.u32 %11, %11, %23;"
-      : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
-        "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11])
-      : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]),
-        "r"(b[9]), "r"(b[10]), "r"(b[11]));
-}
-
-__device__ __forceinline__ void wide_sub(uint32_t (&a)[kWideLimbs], const uint32_t (&b)[kWideLimbs]) {
-  asm("sub.cc.u32 %0, %0, %12;\n\t"
-      "subc.cc.u32 %1, %1, %13;\n\t"
-      "subc.cc.u32 %2, %2, %14;\n\t"
-      "subc.cc.u32 %3, %3, %15;\n\t"
-      "subc.cc.u32 %4, %4, %16;\n\t"
-      "subc.cc.u32 %5, %5, %17;\n\t"
-      "subc.cc.u32 %6, %6, %18;\n\t"
-      "subc.cc.u32 %7, %7, %19;\n\t"
-      "subc.cc.u32 %8, %8, %20;\n\t"
-      "subc.cc.u32 %9, %9, %21;\n\t"
-      "subc.cc.u32 %10, %10, %22;\n\t"
-      "subc.u32 %11, %11, %23;"
-      : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
-        "+r"(a[8]), "+r"(a[9]), "+r"(a[10]), "+r"(a[11])
-      : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]), "r"(b[8]),
-        "r"(b[9]), "r"(b[10]), "r"(b[11]));
-}
-
-// signed compare of two's-complement values whose magnitudes stay below 2^383
-__device__ __forceinline__ int wide_cmp(const uint32_t (&a)[kWideLimbs], const uint32_t (&b)[kWideLimbs]) {
-  uint32_t d[kWideLimbs];
-#pragma unroll
-  for (int i = 0; i < kWideLimbs; i++) d[i] = a[i];
-  wide_sub(d, b);
-  if (d[kWideLimbs - 1] >> 31) return -1;
-  uint32_t any = 0;
-#pragma unroll
-  for (int i = 0; i < kWideLimbs; i++) any |= d[i];
-  return any ? 1 : 0;
-}
-
-__device__ __forceinline__ void wide_load(uint32_t (&a)[kWideLimbs], const uint32_t *p) {
-#pragma unroll
-  for (int i = 0; i < kWideLimbs; i++) a[i] = p[i];
-}
-__device__ __forceinline__ void wide_store(uint32_t *p, const uint32_t (&a)[kWideLimbs]) {
-#pragma unroll
-  for (int i = 0; i < kWideLimbs; i++) p[i] = a[i];
-}
-__device__ __forceinline__ void wide_load_cg(uint32_t (&a)[kWideLimbs], const uint32_t *p) {
-#pragma unroll
-  for (int i = 0; i < kWideLimbs; i++) a[i] = __ldcg(p + i);
-}
-
-// acc += c^A for 0 <= c < 2^21 (limb count grows with the power; loops unroll fully)
-template <int A>
-__device__ __forceinline__ void add_pow(uint32_t (&acc)[kWideLimbs], uint32_t c) {
-  uint32_t p[kWideLimbs];
-  p[0] = c;
-#pragma unroll
-  for (int i = 1; i < kWideLimbs; i++) p[i] = 0;
-#pragma unroll
-  for (int t = 2; t <= A; t++) {
-    uint64_t carry = 0;
-#pragma unroll
-    for (int i = 0; i < kWideLimbs; i++) {
-      if (i < (21 * t + 31) / 32) {
-        const uint64_t v = (uint64_t)p[i] * c + carry;
-        p[i] = (uint32_t)v;
-        carry = v >> 32;
-      }
-    }
-  }
-  wide_add(acc, p);
-}
-
-__device__ __forceinline__ void add_pow_rt(uint32_t (&acc)[kWideLimbs], uint32_t c, uint32_t alpha) {
-  switch (alpha) {
-    case 1: add_pow<1>(acc, c); break;
-    case 2: add_pow<2>(acc, c); break;
-    case 3: add_pow<3>(acc, c); break;
-    case 4: add_pow<4>(acc, c); break;
-    case 5: add_pow<5>(acc, c); break;
-    case 6: add_pow<6>(acc, c); break;
-    case 7: add_pow<7>(acc, c); break;
-    case 8: add_pow<8>(acc, c); break;
-    case 9: add_pow<9>(acc, c); break;
-    case 10: add_pow<10>(acc, c); break;
-    case 11: add_pow<11>(acc, c); break;
-    case 12: add_pow<12>(acc, c); break;
-    case 13: add_pow<13>(acc, c); break;
-    case 14: add_pow<14>(acc, c); break;
-    case 15: add_pow<15>(acc, c); break;
-    default: add_pow<16>(acc, c); break;
-  }
-}
-
-// Correctly rounded (nearest, ties to even) FP64 value of a two's-complement 384-bit integer.
-__device__ double wide_to_double(const uint32_t (&a)[kWideLimbs]) {
-  uint32_t m[kWideLimbs];
-  wide_load(m, a);
-  const bool neg = m[kWideLimbs - 1] >> 31;
-  if (neg) {
-    uint32_t z[kWideLimbs];
-    wide_zero(z);
-    wide_sub(z, m);
-    wide_load(m, z);
-  }
-  int top = -1;
-  for (int i = kWideLimbs - 1; i >= 0; i--)
-    if (m[i]) {
-      top = 32 * i + 31 - __clz(m[i]);
-      break;
-    }
-  if (top < 0) return 0.0;
-  auto bit = [&](int i) -> uint32_t { return (m[i >> 5] >> (i & 31)) & 1u; };
-  double r;
-  if (top <= 52) {
-    r = (double)(((uint64_t)m[1] << 32) | m[0]);
-  } else {
-    const int drop = top - 52;
-    uint64_t mant = 0;
-    for (int i = top; i >= drop; i--) mant = (mant << 1) | bit(i);
-    const uint32_t round = bit(drop - 1);
-    uint32_t sticky = 0;
-    for (int i = drop - 2; i >= 0; i--) sticky |= bit(i);
-    if (round && (sticky || (mant & 1u))) mant++;
-    r = scalbn((double)mant, drop);
-  }
-  return neg ? -r : r;
-}
-
-// Per-k FP32 tables for the next window (Eq. 4 through Sec. 3):
-//   Tp4 = s(|c+4|^a - |c|^a), Tm4 = s(|c-4|^a - |c|^a), Tp2 = s(|c+2|^a - |c|^a), Tm2 = s(|c-2|^a - |c|^a)
-// with s = 2^(-a*e).  Each is (ra - rb) * sum_i ra^i rb^(a-1-i), ra = |c+d|/2^e, rb = |c|/2^e:
-// a sum of non-negative terms, so the relative error stays below (2a+1) 2^-24 (plus an
-// absolute underflow term below 2^-140).
-__device__ __forceinline__ float4 tables_for(int c, uint32_t alpha, float inv2e) {
-  const float rb = fabsf((float)c) * inv2e;
-  const float r0 = fabsf((float)(c + 4)) * inv2e, r1 = fabsf((float)(c - 4)) * inv2e;
-  const float r2 = fabsf((float)(c + 2)) * inv2e, r3 = fabsf((float)(c - 2)) * inv2e;
-  float S0 = 1.f, S1 = 1.f, S2 = 1.f, S3 = 1.f, pb = 1.f;
-  for (uint32_t n = 1; n < alpha; n++) {
-    pb = pb * rb;
-    S0 = fmaf(r0, S0, pb);
-    S1 = fmaf(r1, S1, pb);
-    S2 = fmaf(r2, S2, pb);
-    S3 = fmaf(r3, S3, pb);
-  }
-  return make_float4((r0 - rb) * S0, (r1 - rb) * S1, (r2 - rb) * S2, (r3 - rb) * S3);
-}
-
-__device__ __forceinline__ float absmax4(float4 t) {
-  return fmaxf(fmaxf(fabsf(t.x), fabsf(t.y)), fmaxf(fabsf(t.z), fabsf(t.w)));
-}
-
-// Compensated flush of an FP32 block sum into (hi, lo): hi + lo keeps every flushed value.
-__device__ __forceinline__ void flush_block(float &hi, float &lo, float &blk) {
-  const float s = hi + blk;
-  const float bp = s - hi;
-  const float err = (hi - (s - bp)) + (blk - bp);
-  hi = s;
-  lo += err;
-  blk = 0.f;
-}
-
-template <typename T>
-__device__ __forceinline__ T warp_max(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
 // ------------------------------------------------------------------------------------
 // walk initialisation: Rand(L, SEED) of Alg. 1, C by popcount (Eq. 2), then the
 // update pass in init mode
@@ -257,24 +48,56 @@ __global__ void k_init_bits(WalkDev *hdr, const uint32_t *active) {
   if (idx == 0) W.psl = 0;
 }
 
-// C_k = (L-k) - 2 popc(x[0..L-k) xor x[k..L)) for one k per thread; PSL by atomicMax.
-__global__ void k_autocorr(WalkDev *hdr, const uint32_t *active) {
+// C_k = (L-k) - 2 popc(x[0..L-k) xor x[k..L)) for one k per thread (Eq. 2 on packed bits);
+// PSL by atomicMax.  A block covers 256 consecutive k and streams the packed sequence
+// through shared memory in tiles of 2048 words: for thread k the partner window of word w
+// is funnel(x[w + k/32], x[w + k/32 + 1], k % 32), with a shift that stays fixed, so each
+// iteration costs two broadcast shared loads.
+constexpr int kAcTileWords = 2048;
+
+__global__ void __launch_bounds__(256) k_autocorr(WalkDev *hdr, const uint32_t *active) {
+  __shared__ uint32_t sa[kAcTileWords];
+  __shared__ uint32_t sbw[kAcTileWords + 10];
   WalkDev &W = hdr[active[blockIdx.y]];
-  const int L = (int)W.L;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  const int L = (int)W.L, nw = (int)W.nw;
+  const int k0 = (int)blockIdx.x * 256;
+  if (k0 >= L) return;
+  const uint32_t *bits = W.bits;
+  const int k = k0 + (int)threadIdx.x;
+  const int n = L - k;                          // products of C_k (<= 0 past the end)
+  const int full = n > 0 ? n >> 5 : 0;          // whole words of x[0..n)
+  const int c = (k >> 5) - (k0 >> 5);           // 0..7
+  const int sh = k & 31;
+  const int wend = (L - k0 + 31) >> 5;          // words the block needs at most
+  int cnt = 0;
+  for (int w0 = 0; w0 < wend; w0 += kAcTileWords) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < kAcTileWords + 10; t += 256) {
+      if (t < kAcTileWords) sa[t] = (w0 + t < nw) ? bits[w0 + t] : 0u;
+      const int g = w0 + (k0 >> 5) + t;        // guard words beyond nw read as zero
+      sbw[t] = (g < nw) ? bits[g] : 0u;
+    }
+    __syncthreads();
+    const int wlim = min(full - w0, kAcTileWords);
+    if (wlim > 0) {
+      uint32_t lo = sbw[c];
+      for (int w = 0; w < wlim; w++) {
+        const uint32_t hi = sbw[w + c + 1];
+        cnt += __popc(sa[w] ^ __funnelshift_r(lo, hi, sh));
+        lo = hi;
+      }
+    }
+  }
   int a = 0;
   if (k < L) {
-    const int n = L - k;
-    int cnt = 0;
-    for (int w = 0; 32 * w < n; w++) {
-      uint32_t d = W.bits[w] ^ window32(W.bits, 32 * w + k);
-      const int rem = n - 32 * w;
-      if (rem < 32) d &= (1u << rem) - 1u;
-      cnt += __popc(d);
+    const int rem = n & 31;
+    if (rem) {  // the partial last word of x[0..n)
+      const uint32_t d = bits[full] ^ window32(bits, 32 * full + k);
+      cnt += __popc(d & ((1u << rem) - 1u));
     }
-    const int c = n - 2 * cnt;
-    W.C[k] = c;
-    if (k > 0) a = c < 0 ? -c : c;
+    const int cv = n - 2 * cnt;
+    W.C[k] = cv;
+    if (k > 0) a = cv < 0 ? -cv : cv;
   }
   a = warp_max(a);
   if ((threadIdx.x & 31) == 0 && a > 0) atomicMax(&W.psl, a);
@@ -324,7 +147,37 @@ __device__ __forceinline__ void apply_one(WalkDev &W, uint32_t chunk) {
   float sabs = 0.f;
   uint32_t F[kWideLimbs];
   wide_zero(F);
-  for (int k = k0 + (int)threadIdx.x; k < k1; k += blockDim.x) {
+  // the ordinary step (one move): a lean loop, unrolled so that the loads of several k
+  // are in flight together
+  const int kfirst = k0 + (int)threadIdx.x;
+  int kmove = (mode == kModeMove) ? max(kfirst, 1) : k1;
+  if (mode == kModeMove && kfirst == 0) {
+    W.C[0] = L;
+    if (keep_local) W.C_local[0] = L;
+    kmove = kfirst + (int)blockDim.x;
+  }
+  const int *__restrict__ Cin = W.C;
+  const uint32_t *__restrict__ bits_now = W.bits;
+#pragma unroll 4
+  for (int k = kmove; k < k1; k += blockDim.x) {
+    // Sec. 3: C'_k = C_k - 2 s_j (s_{j+k} + s_{j-k}), absent partners count 0
+    int part = 0;
+    if (kstar + k < L) part += sval(bits_now, kstar + k);
+    if (kstar >= k) part += sval(bits_now, kstar - k);
+    const int c = Cin[k] - 2 * sk * part;
+    W.C[k] = c;
+    if (keep_local) W.C_local[k] = c;
+    const int a = c < 0 ? -c : c;
+    pmax = max(pmax, a);
+    const float4 t = tables_for(c, alpha, inv2e);
+    W.T[k] = t;
+    sabs += absmax4(t);
+    if (a >= thr) {
+      const uint32_t at = atomicAdd(&W.nktau, 1u);
+      W.ktau[at] = make_int2(k, c);
+    }
+  }
+  for (int k = (mode == kModeMove) ? k1 : kfirst; k < k1; k += blockDim.x) {
     int c;
     if (k == 0) {
       c = L;
@@ -480,451 +333,6 @@ __global__ void __launch_bounds__(256) k_apply(WalkDev *hdr, const uint32_t *act
     __syncthreads();  // shared reduction buffers of the previous pair are free
     apply_one(hdr[active[v / nch]], v % nch);
   }
-}
-
-// ------------------------------------------------------------------------------------
-// neighbourhood score, batched form
-//
-// Lanes are window positions.  For neighbour j and shift k, with u = [s_j s_{j+k} = -1]
-// and v = [s_j s_{j-k} = -1]:
-//   both partners present:  delta = +4 if u=v=1, -4 if u=v=0, else 0
-//   one partner present:    delta = +2 if its bit is 1, else -2
-// (k <= kin = min(j, L-1-j): both present; kin < k <= kout = max(j, L-1-j): one; beyond: none.)
-// k runs in super-blocks of 30 = 6 groups of 5.  For each group the block keeps three
-// 32-entry subset-sum tables in shared memory,
-//   W1[b] = sum_{q in b} Tp4_q,  W0[b] = sum_{q in b} Tm4_q,  E[b] = sum_q (b_q ? Tp2_q : Tm2_q),
-// so one lookup scores five (j, k) terms.  Super-block sb owns 2304 bytes (6 groups x 3
-// tables x 32 floats, 128-byte aligned) and entry b of all its tables sits at b ^ (sb & 31):
-// the build (one thread per group, consecutive lanes on consecutive super-blocks) is free
-// of bank conflicts, and a lookup address is ((W >> s) & 0x7C) ^ (base_sb | swizzle) plus a
-// constant: one shift and one three-input logic op.  Regions are decided per warp and per
-// super-block, so the common case runs without per-group tests.
-// ------------------------------------------------------------------------------------
-constexpr int kSbFloats = 576;           // 6 groups x 3 tables x 32 entries
-constexpr int kSbBytes = kSbFloats * 4;  // 2304 bytes = 18 x 128
-
-// tables (rounded up to a 128-byte boundary inside the allocation), two TMA staging
-// buffers of the tile's per-k values, and two ints
-size_t hot_batched_smem(uint32_t tile_sb) { return (size_t)tile_sb * kSbBytes + 2 * (size_t)tile_sb * kSbK * 16 + 256; }
-
-// ---- TMA bulk copies and mbarriers (sm_90 and later) ----
-__device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
-}
-// global -> shared bulk copy (16-byte aligned addresses, size a multiple of 16) signalling mbar
-__device__ __forceinline__ void tma_load_1d(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar) {
-  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-               "l"(src), "r"(bytes), "r"(mbar)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
-  uint32_t done;
-  asm volatile(
-      "{\n .reg .pred P1;\n mbarrier.try_wait.parity.shared::cta.b64 P1, [%1], %2;\n selp.b32 %0, 1, 0, P1;\n}"
-      : "=r"(done)
-      : "r"(mbar), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-// bounded wait: false if the phase did not complete within the iteration limit
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity, int limit = 1 << 20) {
-  for (int it = 0; it < limit; it++)
-    if (mbar_try_wait(mbar, parity)) return true;
-  return false;
-}
-
-template <int OFF>
-__device__ __forceinline__ float lds_at(uint32_t addr) {
-  float v;
-  asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v) : "r"(addr), "n"(OFF));
-  return v;
-}
-
-// 5-bit field Q of w, times 4 (a byte offset in bits 2..6)
-template <int Q>
-__device__ __forceinline__ uint32_t field4(uint32_t w) {
-  if constexpr (Q == 0)
-    return (w << 2) & 0x7Cu;
-  else
-    return (w >> (5 * Q - 2)) & 0x7Cu;
-}
-
-__device__ __forceinline__ uint32_t window32_ro(const uint32_t *__restrict__ bits, int pos) {
-  const int w = pos >> 5;
-  return __funnelshift_r(__ldg(bits + w), __ldg(bits + w + 1), pos & 31);
-}
-
-// tables of group q of super-block sb of the tile (first k of the group: kg)
-// (the tile's per-k values come from the shared staging buffer Ts, entry kg - kt0)
-__device__ __forceinline__ void build_group(float *tab, int sb, int q, const float4 *Ts, int kt0, int kg, int L) {
-  float tp4[5], tm4[5], tp2[5], tm2[5];
-#pragma unroll
-  for (int t = 0; t < 5; t++) {
-    const int k = kg + t;
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (k < L) v = Ts[k - kt0];
-    tp4[t] = v.x;
-    tm4[t] = v.y;
-    tp2[t] = v.z;
-    tm2[t] = v.w;
-  }
-  // low two bits and high three bits summed separately: every entry is a tree of depth <= 3
-  float lo1[4], lo0[4], loe[4], hi1[8], hi0[8], hie[8];
-  lo1[0] = 0.f, lo1[1] = tp4[0], lo1[2] = tp4[1], lo1[3] = tp4[0] + tp4[1];
-  lo0[0] = 0.f, lo0[1] = tm4[0], lo0[2] = tm4[1], lo0[3] = tm4[0] + tm4[1];
-#pragma unroll
-  for (int b = 0; b < 4; b++) loe[b] = ((b & 1) ? tp2[0] : tm2[0]) + ((b & 2) ? tp2[1] : tm2[1]);
-  {
-    const float a23 = tp4[2] + tp4[3], b23 = tm4[2] + tm4[3];
-    hi1[0] = 0.f, hi1[1] = tp4[2], hi1[2] = tp4[3], hi1[3] = a23;
-    hi1[4] = tp4[4], hi1[5] = tp4[2] + tp4[4], hi1[6] = tp4[3] + tp4[4], hi1[7] = a23 + tp4[4];
-    hi0[0] = 0.f, hi0[1] = tm4[2], hi0[2] = tm4[3], hi0[3] = b23;
-    hi0[4] = tm4[4], hi0[5] = tm4[2] + tm4[4], hi0[6] = tm4[3] + tm4[4], hi0[7] = b23 + tm4[4];
-  }
-#pragma unroll
-  for (int b = 0; b < 4; b++) {
-    const float p = ((b & 1) ? tp2[2] : tm2[2]) + ((b & 2) ? tp2[3] : tm2[3]);
-    hie[b] = p + tm2[4];
-    hie[b + 4] = p + tp2[4];
-  }
-  float *base = tab + sb * kSbFloats + q * 96;
-  const int sw = sb & 31;
-#pragma unroll
-  for (int b = 0; b < 32; b++) {
-    const int lo = b & 3, hi = b >> 2;
-    base[b ^ sw] = lo == 0 ? hi1[hi] : (hi == 0 ? lo1[lo] : lo1[lo] + hi1[hi]);
-    base[32 + (b ^ sw)] = lo == 0 ? hi0[hi] : (hi == 0 ? lo0[lo] : lo0[lo] + hi0[hi]);
-    base[64 + (b ^ sw)] = loe[lo] + hie[hi];
-  }
-}
-
-// exact per-term contribution used where a group straddles a region boundary
-__device__ __forceinline__ float term_slow(const float4 *__restrict__ T, int k, int kin, int kout, uint32_t U,
-                                           uint32_t V, bool plus_side, int t) {
-  if (k > kout) return 0.f;
-  const float4 tv = __ldg(T + k);
-  const uint32_t u = (U >> t) & 1u, v = (V >> t) & 1u;
-  if (k <= kin) return (u & v) ? tv.x : ((u | v) ? 0.f : tv.y);
-  const uint32_t e = plus_side ? u : v;
-  return e ? tv.z : tv.w;
-}
-
-// one group of a super-block where lanes may sit in different regions
-template <int Q>
-__device__ __forceinline__ void group_generic(float &a0, float &a1, uint32_t bsw, uint32_t W1, uint32_t W0,
-                                              uint32_t E, uint32_t U, uint32_t V, int ka, int kin, int kout,
-                                              bool plus_side, const float4 *__restrict__ T) {
-  const int kg = ka + 5 * Q;
-  if (kg + 4 <= kin) {
-    a0 += lds_at<Q * 384>(field4<Q>(W1) ^ bsw);
-    a1 += lds_at<Q * 384 + 128>(field4<Q>(W0) ^ bsw);
-  } else if (kg > kin && kg + 4 <= kout) {
-    a0 += lds_at<Q * 384 + 256>(field4<Q>(E) ^ bsw);
-  } else if (kg <= kout) {
-#pragma unroll
-    for (int t = 0; t < 5; t++) a1 += term_slow(T, kg + t, kin, kout, U, V, plus_side, 5 * Q + t);
-  }
-}
-
-// Exact neighbour PSL over the near-peak list: max_k |C_k + delta_jk| for |C_k| >= PSL - 8.
-__device__ __forceinline__ int neighbour_psl(const WalkDev &W, const int2 *list, int n, int j, int L, int sj,
-                                             int floor_c, int cur) {
-  for (int q = 0; q < n; q++) {
-    const int2 e = list[q];
-    const int k = e.x, c = e.y;
-    if ((c < 0 ? -c : c) < floor_c) continue;
-    int part = 0;
-    if (j + k < L) part += sval(W.bits, j + k);
-    if (j >= k) part += sval(W.bits, j - k);
-    const int cn = c - 2 * sj * part;
-    cur = max(cur, cn < 0 ? -cn : cn);
-  }
-  return cur;
-}
-
-// One super-block where every lane has both partners for all 30 shifts.
-__device__ __forceinline__ void sb_interior(float &a0, float &a1, const uint32_t *__restrict__ bits, int pos_u,
-                                            int pos_v, uint32_t M, uint32_t bsw) {
-  const uint32_t U = window32_ro(bits, pos_u);
-  const uint32_t V = __brev(window32_ro(bits, pos_v));
-  const uint32_t W1 = (U ^ M) & (V ^ M), W0 = ~((U ^ M) | (V ^ M));
-  a0 += lds_at<0 * 384>(field4<0>(W1) ^ bsw);
-  a1 += lds_at<0 * 384 + 128>(field4<0>(W0) ^ bsw);
-  a0 += lds_at<1 * 384>(field4<1>(W1) ^ bsw);
-  a1 += lds_at<1 * 384 + 128>(field4<1>(W0) ^ bsw);
-  a0 += lds_at<2 * 384>(field4<2>(W1) ^ bsw);
-  a1 += lds_at<2 * 384 + 128>(field4<2>(W0) ^ bsw);
-  a0 += lds_at<3 * 384>(field4<3>(W1) ^ bsw);
-  a1 += lds_at<3 * 384 + 128>(field4<3>(W0) ^ bsw);
-  a0 += lds_at<4 * 384>(field4<4>(W1) ^ bsw);
-  a1 += lds_at<4 * 384 + 128>(field4<4>(W0) ^ bsw);
-  a0 += lds_at<5 * 384>(field4<5>(W1) ^ bsw);
-  a1 += lds_at<5 * 384 + 128>(field4<5>(W0) ^ bsw);
-}
-
-// One super-block where every lane has exactly one partner for all 30 shifts.
-__device__ __forceinline__ void sb_edge(float &a0, float &a1, const uint32_t *__restrict__ bits, int pos,
-                                        bool plus_side, uint32_t M, uint32_t bsw) {
-  const uint32_t w = window32_ro(bits, pos);
-  const uint32_t E = (plus_side ? w : __brev(w)) ^ M;
-  a0 += lds_at<0 * 384 + 256>(field4<0>(E) ^ bsw);
-  a1 += lds_at<1 * 384 + 256>(field4<1>(E) ^ bsw);
-  a0 += lds_at<2 * 384 + 256>(field4<2>(E) ^ bsw);
-  a1 += lds_at<3 * 384 + 256>(field4<3>(E) ^ bsw);
-  a0 += lds_at<4 * 384 + 256>(field4<4>(E) ^ bsw);
-  a1 += lds_at<5 * 384 + 256>(field4<5>(E) ^ bsw);
-}
-
-// One super-block where region boundaries fall inside it for some lane.
-__device__ __forceinline__ void sb_generic(float &a0, float &a1, const uint32_t *__restrict__ bits,
-                                           const float4 *__restrict__ T, int j, int ka, int kin, int kout,
-                                           bool plus_side, uint32_t M, uint32_t bsw, int cap_u) {
-  if (ka > kout) return;
-  const uint32_t U = window32_ro(bits, min(j + ka, cap_u)) ^ M;
-  const uint32_t V = __brev(window32_ro(bits, max(j - ka - 31, -64))) ^ M;
-  const uint32_t W1 = U & V, W0 = ~(U | V), E = plus_side ? U : V;
-  group_generic<0>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-  group_generic<1>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-  group_generic<2>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-  group_generic<3>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-  group_generic<4>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-  group_generic<5>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-}
-
-__device__ __forceinline__ void flush2(float &hi, float &lo, float &a0, float &a1) {
-  float blk = a0 + a1;
-  a0 = a1 = 0.f;
-  flush_block(hi, lo, blk);
-}
-
-// number of super-blocks sb >= 0 of a tile starting at kt0 with kt0 + 30 sb + off <= bound
-__device__ __forceinline__ int sb_count(int bound, int kt0, int off, int nsb) {
-  const int d = bound - kt0 - off;
-  return d < 0 ? 0 : min(nsb, d / kSbK + 1);
-}
-
-// Scores one work item (a block of window positions, possibly one k-chunk of them).
-// Returns false when a staged copy timed out: the block must then stop taking work.
-template <int NT, int NSB>
-__device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem it) {
-  static_assert(NSB <= 32, "the per-super-block swizzle assumes at most 32 super-blocks per tile");
-  extern __shared__ __align__(128) float smem_raw[];
-  __shared__ __align__(8) uint64_t s_mbar[2];
-  const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(smem_raw);
-  const uint32_t tab_s = (raw_s + 127u) & ~127u;  // lookups OR a swizzle into the low 7 bits
-  float *tab = smem_raw + (tab_s - raw_s) / 4;
-  constexpr int kTileK = NSB * kSbK;
-  float4 *stage = reinterpret_cast<float4 *>(tab + NSB * kSbFloats);  // 2 x kTileK staged T values
-  const uint32_t stage_s = tab_s + NSB * kSbBytes;
-  int *s_kmax = reinterpret_cast<int *>(stage + 2 * kTileK);
-  int *s_timeout = s_kmax + 1;
-  const uint32_t mbar_s = (uint32_t)__cvta_generic_to_shared(s_mbar);
-  WalkDev &W = hdr[it.slot];
-  if (W.status != kRunning) return true;
-  const int L = (int)W.L, N = (int)W.N;
-  const uint32_t *__restrict__ bits = W.bits;
-  const float4 *__restrict__ T = W.T;
-  const int i = (int)it.i0 + (int)threadIdx.x;  // window position, 1-based
-  const bool live = i <= N;
-  // lanes past the end of the window shadow the last neighbour (their sums are discarded),
-  // so every lane of a partly filled warp stays inside the regions of a real neighbour
-  const int j = (int)(((uint64_t)W.start + (uint64_t)min(i, N)) % (uint64_t)L);
-  const bool warp_live = (int)it.i0 + (int)(threadIdx.x & ~31u) <= N;
-  const int kin = min(j, L - 1 - j), kout = max(j, L - 1 - j);
-  const bool plus_side = j < L - 1 - j;
-  const uint32_t M = getbit(bits, j) ? 0xffffffffu : 0u;
-  const int cap_u = 32 * (int)W.nw;
-  const int w_kin_lo = __reduce_min_sync(0xffffffffu, kin);
-  const int w_kin_hi = __reduce_max_sync(0xffffffffu, kin);
-  const int w_kout_lo = __reduce_min_sync(0xffffffffu, kout);
-  const int w_kout_hi = warp_live ? __reduce_max_sync(0xffffffffu, kout) : 0;
-  if (threadIdx.x == 0) {
-    *s_kmax = 0;
-    *s_timeout = 0;
-    mbar_init(mbar_s, 1);
-    mbar_init(mbar_s + 8, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if ((threadIdx.x & 31) == 0) atomicMax(s_kmax, w_kout_hi);
-  __syncthreads();
-  const int kmax = *s_kmax;
-  // tiles of this block: all of them, or those of its k-chunk when the k range is split
-  const int tiles_per_chunk = (int)W.kchunk_sb / NSB;
-  const int tile_lo = W.ksplit > 1 ? (int)it.kc * tiles_per_chunk : 0;
-  const int tile_hi = W.ksplit > 1 ? min((kmax + kTileK - 1) / kTileK, tile_lo + tiles_per_chunk)
-                                   : (kmax + kTileK - 1) / kTileK;
-  const int ntiles = max(0, tile_hi - tile_lo);
-  // TMA bulk copy of tile t's per-k values T[kt0 .. kt0 + kTileK) (those below L) into buffer t & 1
-  auto stage_tile = [&](int t) {
-    const int kt0 = 1 + (tile_lo + t) * kTileK;
-    const uint32_t bytes = 16u * (uint32_t)min(kTileK, L - kt0);
-    const uint32_t mb = mbar_s + 8u * (t & 1);
-    fence_proxy_async();
-    mbar_expect_tx(mb, bytes);
-    tma_load_1d(stage_s + (uint32_t)((t & 1) * kTileK * 16), T + kt0, bytes, mb);
-  };
-  // test hook: no copy is issued, so every wait below runs out (short limit) and the walk
-  // is marked failed; nothing is left in flight
-  const bool stall = W.inject_stall != 0;
-  const int wait_limit = stall ? 64 : (1 << 20);
-  if (threadIdx.x == 0 && ntiles > 0 && !stall) stage_tile(0);
-
-  float hi = 0.f, lo = 0.f, a0 = 0.f, a1 = 0.f;
-  for (int tile = 0; tile < ntiles; tile++) {
-    const int kt0 = 1 + (tile_lo + tile) * kTileK;
-    __syncthreads();  // previous tile fully consumed (tables, and the staging buffer reused below)
-    if (threadIdx.x == 0 && tile + 1 < ntiles && !stall) stage_tile(tile + 1);
-    if ((int)threadIdx.x < 6 * NSB) {
-      if (!mbar_wait_bounded(mbar_s + 8u * (tile & 1), (uint32_t)(tile >> 1) & 1u, wait_limit)) *s_timeout = 1;
-      const float4 *Ts = stage + (tile & 1) * kTileK;
-      for (int t = threadIdx.x; t < 6 * NSB; t += NT) {
-        const int sb = t % NSB, q = t / NSB;
-        build_group(tab, sb, q, Ts, kt0, kt0 + sb * kSbK + 5 * q, L);
-      }
-    }
-    __syncthreads();
-    // warp-uniform phases of this tile, in increasing k:
-    //   [0, n_int)        every lane interior        (ka + 29 <= min kin)
-    //   [n_int, e0)       generic                   (around the kin boundaries)
-    //   [e0, n_edge)      every lane one partner     (ka > max kin, ka + 29 <= min kout)
-    //   [n_edge, n_all)   generic                   (around the kout boundaries)
-    const int n_all = sb_count(w_kout_hi, kt0, 0, NSB);
-    const int n_int = min(sb_count(w_kin_lo, kt0, kSbK - 1, NSB), n_all);
-    const int e0 = max(n_int, min(n_all, sb_count(w_kin_hi, kt0, 0, NSB)));
-    const int n_edge = max(e0, min(n_all, sb_count(w_kout_lo, kt0, kSbK - 1, NSB)));
-    const uint32_t bsw0 = tab_s;  // super-block sb: base + 2304 sb, swizzle sb << 2
-    int sb = 0;
-    {
-      int pu = j + kt0, pv = j - kt0 - 31;
-      uint32_t bsw = bsw0;
-      for (; sb + 1 < n_int; sb += 2) {
-        sb_interior(a0, a1, bits, pu, pv, M, bsw);
-        sb_interior(a0, a1, bits, pu + kSbK, pv - kSbK, M, bsw + (kSbBytes + 4));
-        flush2(hi, lo, a0, a1);
-        pu += 2 * kSbK, pv -= 2 * kSbK, bsw += 2 * (kSbBytes + 4);
-      }
-      if (sb < n_int) {
-        sb_interior(a0, a1, bits, pu, pv, M, bsw);
-        flush2(hi, lo, a0, a1);
-        sb++;
-      }
-    }
-    for (; sb < e0; sb++) {
-      sb_generic(a0, a1, bits, T, j, kt0 + sb * kSbK, kin, kout, plus_side, M, bsw0 + sb * (kSbBytes + 4), cap_u);
-      flush2(hi, lo, a0, a1);
-    }
-    {
-      const int step = plus_side ? kSbK : -kSbK;
-      int pe = plus_side ? j + kt0 + sb * kSbK : j - kt0 - sb * kSbK - 31;
-      uint32_t bsw = bsw0 + sb * (kSbBytes + 4);
-      for (; sb + 1 < n_edge; sb += 2) {
-        sb_edge(a0, a1, bits, pe, plus_side, M, bsw);
-        sb_edge(a0, a1, bits, pe + step, plus_side, M, bsw + (kSbBytes + 4));
-        flush2(hi, lo, a0, a1);
-        pe += 2 * step, bsw += 2 * (kSbBytes + 4);
-      }
-      if (sb < n_edge) {
-        sb_edge(a0, a1, bits, pe, plus_side, M, bsw);
-        flush2(hi, lo, a0, a1);
-        sb++;
-      }
-    }
-    for (; sb < n_all; sb++) {
-      sb_generic(a0, a1, bits, T, j, kt0 + sb * kSbK, kin, kout, plus_side, M, bsw0 + sb * (kSbBytes + 4), cap_u);
-      flush2(hi, lo, a0, a1);
-    }
-  }
-  if (*s_timeout) {
-    // a staged copy never arrived: give every copy of this block one more bounded wait,
-    // then mark the walk failed instead of using its scores
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      if (!stall)
-        for (int t = max(0, ntiles - 2); t < ntiles; t++) mbar_wait_bounded(mbar_s + 8u * (t & 1), (uint32_t)(t >> 1) & 1u);
-      W.error = (uint32_t)-5;  // PSL_ETIMEOUT of the library header
-      W.status = kError;
-    }
-    return stall;  // after a real timeout a copy may still be in flight: stop using this block
-  }
-  if (!live) return true;
-  if (W.ksplit > 1) {
-    W.score_part[(size_t)it.kc * N + (i - 1)] = hi + lo;
-    if (it.kc != 0) return true;
-  } else {
-    W.score[i - 1] = hi + lo;
-  }
-
-  // exact neighbour PSL, only when some neighbour may beat psl_best
-  int pj = INT_MAX;
-  if (W.ktau_on) {
-    const int sj = M ? -1 : 1;
-    pj = neighbour_psl(W, W.ktau, (int)W.nktau, j, L, sj, W.psl - 8, 0);
-  }
-  W.pslj[i - 1] = pj;
-  return true;
-}
-
-// Persistent: every block takes work items one by one from the schedule's counter
-// (longest walks first in the item list).
-template <int NT, int NSB>
-__global__ void __launch_bounds__(NT, 1024 / NT) k_hot_batched(WalkDev *hdr, const HotItem *items, Schedule *sched) {
-  __shared__ uint32_t s_item;
-  for (;;) {
-    __syncthreads();  // the previous item's shared memory is free
-    if (threadIdx.x == 0) s_item = atomicAdd(&sched->hot_next, 1u);
-    __syncthreads();
-    const uint32_t item = s_item;
-    if (item >= sched->nitems) break;
-    if (!hot_one<NT, NSB>(hdr, items[item])) break;
-  }
-}
-
-// ------------------------------------------------------------------------------------
-// neighbourhood score, plain form: one thread per neighbour, every term accumulated
-// on its own (the execution model of the paper's GPU solver)
-// ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_hot_plain(WalkDev *hdrp) {
-  const WalkDev &W = *hdrp;
-  const int L = (int)W.L, N = (int)W.N;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  if (i > N) return;
-  const uint32_t *bits = W.bits;
-  const float4 *T = W.T;
-  const int j = (int)(((uint64_t)W.start + (uint64_t)i) % (uint64_t)L);
-  const int kin = min(j, L - 1 - j), kout = max(j, L - 1 - j);
-  const bool plus_side = j < L - 1 - j;
-  const uint32_t M = getbit(bits, j) ? 0xffffffffu : 0u;
-  const int cap_u = 32 * (int)W.nw;
-  float hi = 0.f, lo = 0.f, blk = 0.f;
-  for (int ka = 1; ka <= kout; ka += kSbK) {
-    const uint32_t U = window32(bits, min(j + ka, cap_u)) ^ M;
-    const uint32_t V = __brev(window32(bits, max(j - ka - 31, -64))) ^ M;
-    const int kend = min(ka + kSbK - 1, kout);
-    for (int k = ka; k <= kend; k++) {
-      const int t = k - ka;
-      const float4 tv = T[k];
-      const uint32_t u = (U >> t) & 1u, v = (V >> t) & 1u;
-      if (k <= kin) {
-        if (u & v)
-          blk += tv.x;
-        else if (!(u | v))
-          blk += tv.y;
-      } else {
-        blk += (plus_side ? u : v) ? tv.z : tv.w;
-      }
-    }
-    flush_block(hi, lo, blk);
-  }
-  W.score[i - 1] = hi + lo;
-  int pj = INT_MAX;
-  if (W.ktau_on) pj = neighbour_psl(W, W.ktau, (int)W.nktau, j, L, M ? -1 : 1, W.psl - 8, 0);
-  W.pslj[i - 1] = pj;
 }
 
 // ------------------------------------------------------------------------------------
@@ -1338,7 +746,6 @@ __global__ void __launch_bounds__(256) k_decide(WalkDev *hdr, const uint32_t *ac
 // ------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------
-static uint32_t g_hot_blocks_per_sm[3][2];  // occupancy of every variant, measured at set-up
 // resident blocks per SM of the other persistent kernels (one wave each)
 static uint32_t g_apply_per_sm = 4, g_select_per_sm = 1, g_recheck_per_sm = 3, g_decide_per_sm = 4;
 
@@ -1365,20 +772,6 @@ cudaError_t launch_apply(const LaunchCtx &c) {
   return cudaGetLastError();
 }
 
-using HotFn = void (*)(WalkDev *, const HotItem *, Schedule *);
-
-static int variant_index(uint32_t threads) { return threads == 512 ? 2 : (threads == 128 ? 0 : 1); }
-
-static HotFn hot_variant(uint32_t threads, uint32_t tile_sb) {
-  if (threads == 512) return tile_sb == 16 ? k_hot_batched<512, 16> : k_hot_batched<512, 32>;
-  if (threads == 128) return tile_sb == 16 ? k_hot_batched<128, 16> : k_hot_batched<128, 32>;
-  return tile_sb == 16 ? k_hot_batched<256, 16> : k_hot_batched<256, 32>;
-}
-
-bool hot_config_supported(uint32_t threads, uint32_t tile_sb) {
-  return (threads == 128 || threads == 256 || threads == 512) && (tile_sb == 16 || tile_sb == 32);
-}
-
 static cudaError_t blocks_per_sm(const void *f, int threads, uint32_t *out) {
   int nb = 0;
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, threads, 0);
@@ -1392,16 +785,8 @@ static cudaError_t prepare_kernels_once() {
   if (e0 == cudaSuccess) e0 = blocks_per_sm((const void *)k_recheck, 256, &g_recheck_per_sm);
   if (e0 == cudaSuccess) e0 = blocks_per_sm((const void *)k_decide, 256, &g_decide_per_sm);
   if (e0 != cudaSuccess) return e0;
-  for (uint32_t t : {128u, 256u, 512u})
-    for (uint32_t sb : {16u, 32u}) {
-      HotFn f = hot_variant(t, sb);
-      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hot_batched_smem(sb));
-      if (e != cudaSuccess) return e;
-      int nb = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, (int)t, hot_batched_smem(sb));
-      if (e != cudaSuccess) return e;
-      g_hot_blocks_per_sm[variant_index(t)][sb == 32 ? 1 : 0] = (uint32_t)(nb > 0 ? nb : 1);
-    }
+  e0 = prepare_hot_kernels();
+  if (e0 != cudaSuccess) return e0;
   return cudaSuccess;
 }
 
@@ -1412,18 +797,6 @@ cudaError_t prepare_kernels() {
   static cudaError_t result = cudaSuccess;
   std::call_once(once, [] { result = prepare_kernels_once(); });
   return result;
-}
-
-cudaError_t launch_hot_batched(const LaunchCtx &c) {
-  const uint32_t per_sm = g_hot_blocks_per_sm[variant_index(c.hot_threads)][c.hot_tile_sb == 32 ? 1 : 0];
-  hot_variant(c.hot_threads, c.hot_tile_sb)<<<per_sm * c.sm_count, c.hot_threads, hot_batched_smem(c.hot_tile_sb),
-                                              c.stream>>>(c.hdr, c.items, c.sched);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_hot_plain(WalkDev *hdr_one, uint32_t N, cudaStream_t s) {
-  k_hot_plain<<<(N + 127) / 128, 128, 0, s>>>(hdr_one);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_select(const LaunchCtx &c) {
