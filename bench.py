@@ -184,7 +184,7 @@ def run_reference(args):
 def kernel_source_hash() -> str:
     """Hash of the sources of the neighbourhood kernel (its translation unit and headers)."""
     h = hashlib.sha256()
-    for fn in ("psl_hot.cu", "psl_device.cuh", "psl_internal.h"):
+    for fn in ("psl_hot.cu", "psl_device.cuh"):
         with open(os.path.join(ROOT, "paper_2107_09801_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
@@ -222,6 +222,29 @@ def aggregate(local_ms: float, local_units: int, world: int, dist=None, device=N
     return float(u.item()) / (float(t.item()) / 1000.0), float(t.item())
 
 
+def fp32_error_stats(traces) -> dict:
+    """Worst |FP32 score - exact Delta F| of the chosen moves relative to the rigorous bound B,
+    over consecutive traced steps (the exact F before each step is the previous step's)."""
+    import math
+    worst, worst_rel, n = 0.0, 0.0, 0
+    for tr in traces:
+        prev = None
+        for r in tr:
+            v = 0
+            for i, w in enumerate(r["value_exact"]):
+                v |= int(w) << (32 * i)
+            if v >> 383:
+                v -= 1 << 384
+            if prev is not None:
+                exact = math.ldexp(float(v - prev), -int(r["alpha"]) * int(r["scale_e"]))
+                err = abs(float(r["score_kstar"]) - exact)
+                worst = max(worst, err / float(r["bound"]))
+                worst_rel = max(worst_rel, err / max(abs(exact), 1e-300))
+                n += 1
+            prev = None if (int(r["flags"]) & 4) else v
+    return {"moves_checked": n, "max_err_over_bound": worst, "max_rel_err": worst_rel}
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -251,7 +274,11 @@ def run_ours(args):
 
     out = {}
     with P.Context(arena_tensor=arena, stream=stream, max_walks=len(specs), device=local) as ctx:
-        ids = [ctx.submit(s.L, s.seed, s.alpha1, s.alpha2, s.budget) for s in specs]
+        # the first walks keep a per-step trace so that the FP32 score error can be stated
+        n_traced = min(8, len(specs))
+        ids = [ctx.submit_ex(s.L, s.seed, s.alpha1, s.alpha2, s.budget, trace_cap=args.warmup + args.steps)
+               if q < n_traced else ctx.submit(s.L, s.seed, s.alpha1, s.alpha2, s.budget)
+               for q, s in enumerate(specs)]
         ctx.step(1)             # admission and initialisation
         if args.hot_threads or args.hot_tile:
             ctx._set_hot(args.hot_threads or 256, args.hot_tile or 32)
@@ -274,6 +301,7 @@ def run_ours(args):
         ms = e0.elapsed_time(e1)
         st = [ctx.poll(i) for i in ids[:4]]
         assert all(s["moves"] == args.warmup + args.steps for s in st)
+        fp32_err = fp32_error_stats([ctx.trace(i, args.warmup + args.steps) for i in ids[:n_traced]])
     flip_evals_rank = len(specs) * N * args.steps
     value, ms_max = aggregate(ms, flip_evals_rank, world, dist, dev)
 
@@ -388,6 +416,7 @@ def run_ours(args):
                                            "(median SM clock sampled in the timed region)",
                              "ops_basis": "2 lane-ops per (neighbour, shift) term, (L-1) terms per flip-eval"},
                 "clocks": clocks, "gpu_launches": launches, "kernels": kernels,
+                "fp32_score_error": fp32_err,
                 "plain": plain,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,
                 "paper_context": {"A100_one_walk_flip_evals_per_s_L131071": PAPER_A100_L131071},

@@ -131,7 +131,8 @@ typedef struct {
   int32_t psl, psl_best, win_psl;
   uint32_t win_psl_j, flags, nflip, ncand;
   float score_kstar, score_min, bound;
-  uint32_t pad[2];          /* explicit padding: the record has no implicit padding (128 bytes) */
+  int32_t scale_e;          /* score_kstar, score_min and bound are in units of 2^(alpha * scale_e) */
+  uint32_t pad;             /* explicit padding: the record has no implicit padding (128 bytes) */
   double value_step;
   uint32_t value_exact[12];
 } psl_trace_rec;

@@ -57,7 +57,7 @@ class psl_kernel_time(ct.Structure):
 TRACE_DTYPE = np.dtype([("step", "<u8"), ("start", "<u4"), ("kstar", "<u4"), ("alpha", "<u4"), ("unimproved", "<u4"),
                         ("psl", "<i4"), ("psl_best", "<i4"), ("win_psl", "<i4"), ("win_psl_j", "<u4"),
                         ("flags", "<u4"), ("nflip", "<u4"), ("ncand", "<u4"), ("score_kstar", "<f4"),
-                        ("score_min", "<f4"), ("bound", "<f4"), ("pad", "<u4", (2,)), ("value_step", "<f8"),
+                        ("score_min", "<f4"), ("bound", "<f4"), ("scale_e", "<i4"), ("pad", "<u4"), ("value_step", "<f8"),
                         ("value_exact", "<u4", (WIDE,))])
 
 assert TRACE_DTYPE.itemsize == 128  # psl_trace_rec has no implicit padding

@@ -36,7 +36,8 @@ struct TraceRec {
   int32_t psl, psl_best, win_psl;
   uint32_t win_psl_j, flags, nflip, ncand;
   float score_kstar, score_min, bound;
-  uint32_t pad[2];                // explicit: value_step starts at byte 72, no implicit padding
+  int32_t scale_e;                // the step's FP32 tables were scaled by 2^(-alpha * scale_e)
+  uint32_t pad;                   // explicit: value_step starts at byte 72, no implicit padding
   double value_step;              // exact F of the chosen neighbour, rounded to FP64
   uint32_t value_exact[kWideLimbs];
 };

@@ -653,6 +653,7 @@ __device__ __forceinline__ void decide_one(WalkDev &W) {
   }
   if (threadIdx.x != 0) return;
 
+  const int32_t e_used = W.e;  // scale of this step's tables, before the next one is chosen
   uint32_t vstep[kWideLimbs], vlocal[kWideLimbs];
   wide_load(vstep, s_best);
   wide_load(vlocal, W.value_local);
@@ -729,6 +730,7 @@ __device__ __forceinline__ void decide_one(WalkDev &W) {
     r.score_kstar = W.score[kstar_i - 1];
     r.score_min = W.score_min;
     r.bound = W.bound;
+    r.scale_e = e_used;
     r.value_step = wide_to_double(vstep);
     wide_store(r.value_exact, vstep);
   }

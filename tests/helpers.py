@@ -105,3 +105,19 @@ def same_decisions(a, b) -> bool:
     """Equality of two GPU traces on every decision field (FP32 filter scores, the bound
     and the candidate count may differ between launch configurations)."""
     return len(a) == len(b) and all(np.array_equal(a[f], b[f]) for f in DECISION_FIELDS)
+
+
+def fp32_error_ratios(trace, F0=None):
+    """|FP32 score of the chosen move - its exact Delta F| / bound B, both in the step's
+    table units 2^(alpha * scale_e), for every step whose previous exact F is known (the
+    first step needs F0; steps right after a phase switch are skipped)."""
+    import math
+    out = []
+    prev = F0
+    for r in trace:
+        v = limbs32_to_int(r["value_exact"])
+        if prev is not None:
+            exact = math.ldexp(float(v - prev), -int(r["alpha"]) * int(r["scale_e"]))
+            out.append(abs(float(r["score_kstar"]) - exact) / float(r["bound"]))
+        prev = None if (r["flags"] & O.SWITCH) else v
+    return out

@@ -336,3 +336,32 @@ def test_serving_by_length_class_matches_oracle(P):
         w.run(req.spec.budget)
         psl, seq = res.psl_best[r]
         assert psl == w.psl_best and np.array_equal(seq, w.sol_best), r
+
+
+# ------------------------------------------------------------------------------------------------
+# precision: the FP32 score of every chosen move stays within the rigorous bound of its exact ΔF
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("form", ["batched", "plain"])
+def test_fp32_scores_within_bound(P, form):
+    from helpers import fp32_error_ratios
+    specs = W.small_specs(seed=13, count=8, L_choices=(255, 1023, 4095, 16383)) + \
+        [W.WalkSpec(L=65535, seed=7, alpha1=4, alpha2=13, budget=6), W.WalkSpec(L=131071, seed=8, alpha1=13,
+                                                                                  alpha2=4, budget=4)]
+    res = run_gpu(P, specs, form=form)
+    ratios = []
+    for spec, (tr, st, _, _) in zip(specs, res):
+        F0 = O.fitness(O.autocorr(O.init_seq(spec.L, spec.seed)), spec.alpha1)[0]
+        r = fp32_error_ratios(tr, F0)
+        assert all(np.isfinite(r)), spec
+        ratios += r
+    assert len(ratios) > 100
+    assert max(ratios) <= 1.0, max(ratios)
+    print(f"{form}: max |FP32 score - exact| / bound over {len(ratios)} moves = {max(ratios):.3e}")
+
+
+def test_plain_and_batched_agree_at_full_size(P):
+    spec = W.WalkSpec(L=131071, seed=3, budget=3)
+    (tb, sb, _, _), = run_gpu(P, [spec], form="batched")
+    (tp, sp, _, _), = run_gpu(P, [spec], form="plain")
+    assert same_decisions(tb, tp)
+    assert np.array_equal(sb["C"], sp["C"]) and np.array_equal(sb["pivot"], sp["pivot"])
