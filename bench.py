@@ -355,6 +355,21 @@ def run_ours(args):
                "d2h_bytes_per_step": (len(specs) * hdr_bytes * args.steps + len(specs) * L) / args.steps,
                "includes": "submit, walk initialisation, steps, status and best-sequence readback"}
 
+    # the small configuration: L = 1023, one walk from seed 1, N = L, 2000 moves, time to budget
+    small = None
+    if args.other_configs and rank == 0:
+        spec1 = W.plain_small().walks[0]
+        small = {"workload": W.plain_small().name, "moves": spec1.budget}
+        for label, kw in (("plain_s", dict(form="plain")), ("batched_graph_s", dict(steps_per_graph=50))):
+            with P.Context(arena_bytes=64 << 20, stream=stream, max_walks=2, device=local, **kw) as c1:
+                wid = c1.submit_ex(spec1.L, spec1.seed, spec1.alpha1, spec1.alpha2, spec1.budget, n_lmt=spec1.n_lmt)
+                torch.cuda.synchronize(dev)
+                t0 = time.perf_counter()
+                c1.run()
+                torch.cuda.synchronize(dev)
+                small[label] = time.perf_counter() - t0
+                small[label.replace("_s", "_psl_best")] = c1.poll(wid)["psl_best"]
+
     # the other batch configurations of the survey: throughput only (a few timed steps each)
     others = None
     if args.other_configs and rank == 0:
@@ -422,6 +437,7 @@ def run_ours(args):
                 "paper_context": {"A100_one_walk_flip_evals_per_s_L131071": PAPER_A100_L131071},
                 "serving": serving,
                 "other_configs": others,
+                "small_config": small,
                 "e2e": e2e}
         if not args.no_cpu_baseline:
             sampler = OracleSampler(L, N, 4)

@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "psl.h"
 #include "psl_internal.h"
 
@@ -768,14 +770,25 @@ static int run_plain(psl_ctx *ctx, uint32_t steps) {
   return PSL_OK;
 }
 
+// NVTX range for the duration of a scope (visible in Nsight timelines)
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 extern "C" int psl_step(psl_ctx *ctx, uint32_t max_moves) {
   if (!ctx) return PSL_EINVAL;
+  NvtxRange r_step("psl_step");
   CK(cudaSetDevice(ctx->cfg.device));
-  int rc = admit(ctx);
-  if (rc) return rc;
-  if (ctx->active_dirty) {
-    rc = rebuild_active(ctx);
+  int rc;
+  {
+    NvtxRange r("psl_step/admit");
+    rc = admit(ctx);
     if (rc) return rc;
+    if (ctx->active_dirty) {
+      rc = rebuild_active(ctx);
+      if (rc) return rc;
+    }
   }
   // never run past the largest remaining budget
   uint64_t remaining = 0;
@@ -785,10 +798,16 @@ extern "C" int psl_step(psl_ctx *ctx, uint32_t max_moves) {
     remaining = std::max<uint64_t>(remaining, h.budget > done ? h.budget - done : 0);
   }
   const uint32_t steps = (uint32_t)std::min<uint64_t>(max_moves, remaining);
-  rc = ctx->cfg.form == PSL_FORM_PLAIN ? run_plain(ctx, steps) : run_batched(ctx, steps);
-  if (rc) return rc;
-  rc = refresh_headers(ctx);
-  if (rc) return rc;
+  {
+    NvtxRange r("psl_step/steps");
+    rc = ctx->cfg.form == PSL_FORM_PLAIN ? run_plain(ctx, steps) : run_batched(ctx, steps);
+    if (rc) return rc;
+  }
+  {
+    NvtxRange r("psl_step/status");
+    rc = refresh_headers(ctx);
+    if (rc) return rc;
+  }
   int n = (int)ctx->queue.size();
   for (auto &kv : ctx->walks) n += kv.second.state == PSL_RUNNING;
   return n;

@@ -365,3 +365,26 @@ def test_plain_and_batched_agree_at_full_size(P):
     (tp, sp, _, _), = run_gpu(P, [spec], form="plain")
     assert same_decisions(tb, tp)
     assert np.array_equal(sb["C"], sp["C"]) and np.array_equal(sb["pivot"], sp["pivot"])
+
+
+# ------------------------------------------------------------------------------------------------
+# restart-from-best rounds: each round restarts every walk from the previous round's best
+# ------------------------------------------------------------------------------------------------
+def test_restart_rounds_match_oracle(P):
+    from paper_2107_09801_gb300.rounds import restart_rounds
+    L, n, rounds, budget = 255, 3, 3, 40
+    with P.Context(arena_bytes=1 << 26, max_walks=8) as ctx:
+        hist = restart_rounds(ctx, L, n, rounds, budget, alpha1=4, alpha2=13, seed0=100, ls_lmt=5)
+    start = None
+    for r in range(rounds):
+        found = []
+        for i in range(n):
+            spec = W.WalkSpec(L=L, seed=100 + r * n + i, alpha1=4, alpha2=13, budget=budget, ls_lmt=5)
+            w = oracle_walk(spec, s0=start)
+            w.run(budget)
+            found.append((w.psl_best, w.sol_best.copy()))
+        i_best = min(range(n), key=lambda i: (found[i][0], i))
+        start = found[i_best][1]
+        assert hist[r].psl_best == found[i_best][0] and hist[r].walk == i_best
+        assert np.array_equal(hist[r].sequence, start)
+    assert hist[-1].psl_best <= hist[0].psl_best
