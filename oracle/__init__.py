@@ -51,7 +51,7 @@ class _State(ct.Structure):
                 ("C", ct.c_void_p), ("value_local", ct.c_uint64 * WL), ("F", ct.c_uint64 * WL),
                 ("alpha", ct.c_uint32), ("unimproved", ct.c_uint32), ("psl", ct.c_int32),
                 ("psl_best", ct.c_int32), ("rng_ctr", ct.c_uint64), ("steps", ct.c_uint64),
-                ("near_ties", ct.c_uint64)]
+                ("near_ties", ct.c_uint64), ("fbest_seq", ct.c_void_p), ("F_best", ct.c_uint64 * WL)]
 
 
 TRACE_DTYPE = np.dtype([("step", "<u8"), ("start", "<u4"), ("kstar", "<u4"), ("alpha", "<u4"),
@@ -204,7 +204,9 @@ class Walk:
         self.local_best = np.zeros(L, dtype=np.int8)
         self.sol_best = np.zeros(L, dtype=np.int8)
         self.C = np.zeros(L, dtype=np.int32)
+        self.fbest_seq = np.zeros(L, dtype=np.int8)
         self._st = _State(_ptr(self.s), _ptr(self.local_best), _ptr(self.sol_best), _ptr(self.C))
+        self._st.fbest_seq = _ptr(self.fbest_seq)
         self._pc = p.c()
         rc = lib().orc_init(ct.byref(self._pc), ct.byref(self._st))
         if rc != 0:
@@ -250,6 +252,11 @@ class Walk:
     def F(self) -> int:
         return limbs_to_int(self._st.F)
 
+    @property
+    def F_best(self) -> int:
+        """Lowest exact F over the visited pivots (kept only when alpha1 == alpha2)."""
+        return limbs_to_int(self._st.F_best)
+
     def load_state(self, *, s, local_best, sol_best, alpha, unimproved, rng_ctr, value_local=None,
                    psl_best=None, steps=0):
         """Replace the walk state (decision replay from an exported state).  C, PSL and F are
@@ -270,6 +277,9 @@ class Walk:
             self._st.value_local[i] = int(w)
         self._st.psl = psl(self.C)
         self._st.psl_best = psl(autocorr(self.sol_best)) if psl_best is None else psl_best
+        self.fbest_seq[:] = s
+        for i in range(WL):
+            self._st.F_best[i] = self._st.F[i]
 
     def run(self, nsteps: int, mode: int = MODE_INCREMENTAL) -> np.ndarray:
         tr = np.zeros(nsteps, dtype=TRACE_DTYPE)

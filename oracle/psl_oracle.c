@@ -38,6 +38,13 @@
  *     starts as pivot_0.  At a switch local_best is left unchanged.
  *   - The budget counts while-iterations; every iteration makes one move.
  *   - alpha is an integer in 1..16.
+ *   - When alpha1 == alpha2 the objective never changes, so the lowest F over
+ *     every pivot the walk visits (the start, each move, each perturbed pivot
+ *     of a switch; the first one on ties) is kept with its sequence.  With
+ *     alpha = 2 that F is the energy sum C_k^2 of the merit factor
+ *     MF = L^2 / (2 sum C_k^2) defined in Sec. 2.  With alpha1 != alpha2 F
+ *     values of the two phases are not comparable and nothing is kept past
+ *     the start.
  */
 #include <math.h>
 #include <stdint.h>
@@ -284,6 +291,8 @@ typedef struct {
     uint32_t alpha, unimproved;
     int32_t psl, psl_best;
     uint64_t rng_ctr, steps, near_ties;
+    int8_t *fbest_seq;  /* lowest-F pivot when alpha1 == alpha2      */
+    uint64_t F_best[WL];
 } orc_state;
 
 typedef struct {
@@ -318,6 +327,8 @@ ORC_API int orc_init(const orc_params *p, orc_state *st) {
     if (orc_fitness(st->C, L, st->alpha, limbs, NULL, NULL)) return -1;
     memcpy(st->value_local, limbs, sizeof limbs);
     memcpy(st->F, limbs, sizeof limbs);
+    memcpy(st->F_best, limbs, sizeof limbs);
+    memcpy(st->fbest_seq, st->s, L);
     st->unimproved = 0;
     st->psl = orc_psl(st->C, L);
     st->psl_best = st->psl;
@@ -345,6 +356,18 @@ static int neighbour_C(const int8_t *s, const int32_t *C, uint32_t L, uint32_t j
         if (memcmp(Cn, Cchk, sizeof(int32_t) * L) != 0) return -2;
     }
     return 0;
+}
+
+/* Keeps the pivot if its exact F is below the lowest seen (fixed objective only). */
+static void note_pivot(const orc_params *p, orc_state *st) {
+    if (p->alpha1 != p->alpha2) return;
+    wide_t f, b;
+    memcpy(f.w, st->F, sizeof f.w);
+    memcpy(b.w, st->F_best, sizeof b.w);
+    if (wide_cmp(&f, &b) < 0) {
+        memcpy(st->F_best, st->F, sizeof st->F_best);
+        memcpy(st->fbest_seq, st->s, p->L);
+    }
 }
 
 /* Runs nsteps iterations of the while loop of Alg. 1.  trace may be NULL. */
@@ -434,6 +457,7 @@ ORC_API int orc_run(const orc_params *p, orc_state *st, uint64_t nsteps, int mod
         memcpy(st->C, Cn, sizeof(int32_t) * L);
         st->s[kstar] = (int8_t)-st->s[kstar];
         memcpy(st->F, value_step.w, sizeof st->F);
+        note_pivot(p, st);
 
         wide_t value_local;
         memcpy(value_local.w, st->value_local, sizeof value_local.w);
@@ -467,6 +491,7 @@ ORC_API int orc_run(const orc_params *p, orc_state *st, uint64_t nsteps, int mod
                 }
                 memcpy(st->value_local, limbs, sizeof limbs);
                 memcpy(st->F, limbs, sizeof limbs);
+                note_pivot(p, st);
                 st->unimproved = 0;
                 flags |= ORC_SWITCH;
             }

@@ -309,3 +309,69 @@ def test_search_quality_loose():
     psl0 = w.psl
     w.run(300)
     assert w.psl_best < 0.6 * psl0 and w.psl_best < math.sqrt(255)
+
+
+# --------------------------------------------------------------------------------------------
+# fixed objective (alpha1 == alpha2): the lowest-F pivot; alpha = 2 is the merit-factor energy
+# --------------------------------------------------------------------------------------------
+def np_energy(s):
+    """E = sum_{k>=1} C_k^2 by numpy's full correlation (an independent route to Eq. 2)."""
+    c = np.correlate(s.astype(np.int64), s.astype(np.int64), mode="full")[len(s):]
+    return int(np.dot(c, c))
+
+
+@pytest.mark.parametrize("L,alpha", [(31, 2), (63, 2), (100, 2), (45, 3)])
+def test_lowest_f_pivot_is_first_minimum_of_visited_pivots(L, alpha):
+    """No switch (LS_lmt above the budget): the pivots are the start plus one flip per move,
+    so every visited pivot is rebuilt from the move list and scored independently."""
+    p = O.WalkParams(L=L, seed=L + alpha, alpha1=alpha, alpha2=alpha, n_lmt=L, ls_lmt=10**6, flip_lmt=3)
+    w = O.Walk(p)
+    s = w.s.copy()
+    tr = w.run(120)
+    assert not np.any(tr["flags"] & O.SWITCH)
+    pivots = [s.copy()]
+    for r in tr:
+        s[r["kstar"]] = -s[r["kstar"]]
+        pivots.append(s.copy())
+    f = [py_fitness(fft_autocorr(q), alpha) for q in pivots]
+    if alpha == 2:
+        assert f == [np_energy(q) for q in pivots]
+    first = int(np.argmin(f))        # numpy: first index of the minimum
+    assert w.F_best == f[first]
+    assert np.array_equal(w.fbest_seq, pivots[first])
+
+
+@pytest.mark.parametrize("L", [31, 127])
+def test_lowest_energy_with_switches(L):
+    p = O.WalkParams(L=L, seed=3 * L, alpha1=2, alpha2=2, n_lmt=L, ls_lmt=3, flip_lmt=4)
+    w = O.Walk(p)
+    F0 = w.F
+    tr = w.run(200)
+    assert np.any(tr["flags"] & O.SWITCH)
+    assert np.all(tr["alpha"] == 2)
+    steps = [O.limbs_to_int(v) for v in tr["value_exact"]]
+    assert w.F_best <= min([F0] + steps)              # switch pivots may go lower still
+    assert np_energy(w.fbest_seq) == w.F_best
+
+
+def test_lowest_energy_not_kept_when_phases_differ():
+    p = O.WalkParams(L=63, seed=9, alpha1=2, alpha2=5, n_lmt=63, ls_lmt=3, flip_lmt=4)
+    w = O.Walk(p)
+    s0, F0 = w.s.copy(), w.F
+    w.run(60)
+    assert w.F_best == F0 and np.array_equal(w.fbest_seq, s0)
+
+
+def test_barker13_is_a_lowest_energy_start(golden):
+    """Barker-13 has energy 6 (merit factor 169/12), the minimum over all 2^13 sequences
+    (exhaustive search below); a walk started there never leaves it as its lowest pivot."""
+    b = barker13(golden)
+    assert np_energy(b) == 6
+    best = min(np_energy(np.array([1 if (m >> i) & 1 else -1 for i in range(13)], dtype=np.int8))
+               for m in range(1 << 12))   # s_12 = -1 fixed: negation symmetry covers the rest
+    assert best == 6
+    p = O.WalkParams(L=13, seed=1, alpha1=2, alpha2=2, n_lmt=13, ls_lmt=2, flip_lmt=3)
+    w = O.Walk(p, s0=b)
+    assert w.F_best == 6
+    w.run(50)
+    assert w.F_best == 6 and np.array_equal(w.fbest_seq, b)

@@ -28,6 +28,10 @@ MUTATIONS = [
     ("window_off_by_one", "((uint64_t)start + i) % L", "((uint64_t)start + i - 1) % L"),
     ("start_bits_inverted", "s[i] = ((d >> (i % 64)) & 1u) ? -1 : 1;", "s[i] = ((d >> (i % 64)) & 1u) ? 1 : -1;"),
     ("power_off_by_one", "for (uint32_t a = 0; a < alpha; a++)", "for (uint32_t a = 1; a < alpha; a++)"),
+    ("fbest_ties_take_last", "if (wide_cmp(&f, &b) < 0) {", "if (wide_cmp(&f, &b) <= 0) {"),
+    ("fbest_ignores_moves", "memcpy(st->F, value_step.w, sizeof st->F);\n        note_pivot(p, st);",
+     "memcpy(st->F, value_step.w, sizeof st->F);"),
+    ("fbest_kept_with_two_alphas", "if (p->alpha1 != p->alpha2) return;", "if (p->alpha1 == 0) return;"),
     ("transposed_pair", "c += (int32_t)s[i] * (int32_t)s[i + k];", "c += (int32_t)s[i] * (int32_t)s[L - 1 - i];"),
 ]
 
