@@ -27,6 +27,8 @@ import tempfile
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -55,6 +57,24 @@ def parse():
     ap.add_argument("--other-configs", type=int, default=1, help="also time the L=16383 x 4096 and L=1048575 x 148 batches")
     ap.add_argument("--serving", type=int, default=24, help="requests of the serving trace to run (0: skip)")
     ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--serving-study", type=int, default=0,
+                    help="run only the serving study on this many requests: the trace at --serving-rate "
+                         "(saturated), then at 0.8x the measured capacity; prints its own JSON line")
+    ap.add_argument("--serving-study-light", type=int, default=300,
+                    help="requests of the 0.8x-capacity leg of the serving study")
+    ap.add_argument("--serving-compare", type=int, default=0,
+                    help="serving study: also run this many requests at --serving-rate under each SM split "
+                         "(fixed, by outstanding work, by live requests)")
+    ap.add_argument("--serving-policy", default="requests", choices=["requests", "work"],
+                    help="SM split between the serving length classes")
+    ap.add_argument("--ablation", action="store_true",
+                    help="run only the control-parameter studies (alpha pairs; LS_lmt x FLIP_lmt) at reduced "
+                         "scale; prints their own JSON line")
+    ap.add_argument("--ablation-L", type=int, default=16383)
+    ap.add_argument("--ablation-runs", type=int, default=30)
+    ap.add_argument("--ablation-nse", type=float, default=1e9, help="sequence evaluations per run, alpha pairs")
+    ap.add_argument("--grid-runs", type=int, default=10)
+    ap.add_argument("--grid-nse", type=float, default=2e8, help="sequence evaluations per run, LS x FLIP grid")
     ap.add_argument("--hot-threads", type=int, default=0, help="force the neighbourhood-kernel block size")
     ap.add_argument("--hot-tile", type=int, default=0, help="force the k-tile (super-blocks of 30)")
     return ap.parse_args()
@@ -374,7 +394,7 @@ def run_ours(args):
     others = None
     if args.other_configs and rank == 0:
         others = {}
-        for wl_o in (W.batch_16383(), W.batch_1048575()):
+        for wl_o, k_o in ((W.batch_16383(), 5), (W.batch_1048575(), 5), (W.labs_1023(), 100)):
             specs_o = list(wl_o.walks)
             need_o = sum(P.psl_walk_bytes(x.L, x.n_lmt, 0) for x in specs_o)
             with P.Context(arena_bytes=int(need_o * 1.1) + (64 << 20), stream=stream, max_walks=len(specs_o),
@@ -390,17 +410,27 @@ def run_ours(args):
                 oc.profile(True)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                oc.step(5)
+                oc.step(k_o)
                 e1.record(stream)
                 torch.cuda.synchronize(dev)
                 prof_o = oc.profile_read()
                 ms_o = e0.elapsed_time(e1)
+                quality = None
+                if specs_o[0].alpha1 == specs_o[0].alpha2 == 2:
+                    # merit factor L^2 / (2 E) of every walk's lowest-energy pivot so far
+                    ids_o = sorted(oc.L_of)
+                    mf = [specs_o[0].L ** 2 / (2.0 * oc.best_fitness(w)[0]) for w in ids_o]
+                    quality = {"moves": 3 + k_o, "merit_factor_mean": float(np.mean(mf)),
+                               "merit_factor_best": float(np.max(mf))}
             Lo, No = specs_o[0].L, specs_o[0].N
             n_hot, hot_ms_o = prof_o.get("hot", (0, 0.0))
-            others[wl_o.name] = {"value": len(specs_o) * No * 5 / (ms_o / 1000.0), "unit": UNIT,
-                                 "ms_per_step": ms_o / 5, "hot_kernel": {"threads": tune_o[0], "tile_superblocks": tune_o[1]},
+            others[wl_o.name] = {"value": len(specs_o) * No * k_o / (ms_o / 1000.0), "unit": UNIT,
+                                 "ms_per_step": ms_o / k_o, "steps": k_o,
+                                 "hot_kernel": {"threads": tune_o[0], "tile_superblocks": tune_o[1]},
                                  "roofline_frac": (len(specs_o) * No * 2 * (Lo - 1)) / (hot_ms_o / max(n_hot, 1) / 1000.0) / peak,
                                  "init_s": t_init, "description": wl_o.description}
+            if quality:
+                others[wl_o.name]["quality"] = quality
 
     # serving: Poisson arrivals of walks with L = 2^m - 1, m uniform in 10..20, continuous batching
     serving = None
@@ -409,11 +439,12 @@ def run_ours(args):
         trace = W.serving_trace(n_requests=args.serving, rate_hz=args.serving_rate)
         arena_s = min(24 << 30, int(sum(P.psl_walk_bytes(r.spec.L, r.spec.n_lmt, 0) for r in trace) * 1.5) + (256 << 20))
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        res = serve_classes(trace, arena_s, sm_count=sms, ctx_kwargs=dict(device=local))
+        res = serve_classes(trace, arena_s, sm_count=sms, ctx_kwargs=dict(device=local),
+                            share_policy=args.serving_policy)
         serving = dict(res.summary(), rate_hz=args.serving_rate, trace="Poisson arrivals, m~U{10..20}, budgets "
                        "~U{100..10^4}, alpha1~U{2..6}, alpha2~U{alpha1+4..13}, request r has seed r",
-                       arena_gb=arena_s / 1e9, classes="L<=2^14 on 12% of SMs, <=2^17 on 30%, <=2^20 on 58%; "
-                       "one stream and host thread each")
+                       arena_gb=arena_s / 1e9, classes="L<=2^14, <=2^17, <=2^20: one context, stream and host "
+                       f"thread each; SMs split by {args.serving_policy} (8-SM floor per busy class)")
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -453,10 +484,103 @@ def run_ours(args):
     return 0
 
 
+def run_serving_study(args):
+    """Serving with continuous batching on one GPU: a finite trace of requests at the trace's
+    arrival rate, far above capacity, so the queue saturates; the capacity in requests/s
+    measured there; then a second trace at 0.8x that capacity, where latency must stay
+    bounded (the later half of the requests is compared with the earlier half)."""
+    import torch
+
+    import paper_2107_09801_gb300 as P
+    from paper_2107_09801_gb300.serving import serve_classes, walk_terms_per_move
+
+    torch.cuda.set_device(0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    desc = ("Poisson arrivals, L=2^m-1 with m~U{10..20}, budgets ~U{100..10^4} moves, alpha1~U{2..6}, "
+            "alpha2~U{alpha1+4..13}, N_lmt 6912, LS_lmt 2000, FLIP_lmt 10, request r has seed r")
+
+    def leg(n, rate, policy=args.serving_policy):
+        trace = W.serving_trace(n_requests=n, rate_hz=rate)
+        arena = min(48 << 30, int(sum(P.psl_walk_bytes(r.spec.L, r.spec.n_lmt, 0) for r in trace) * 1.5) + (256 << 20))
+        clk = ClockSampler(0)
+        clk.start()
+        res = serve_classes(trace, arena, sm_count=sms, share_policy=policy)
+        clocks = clk.stop()
+        terms = sum(r.spec.budget * walk_terms_per_move(r.spec) for r in trace)
+        # requests in arrival order (the trace is generated in arrival order)
+        lat = [res.latency_of[r] for r in range(len(trace)) if r in res.latency_of]
+        half = len(lat) // 2
+        return dict(res.summary(), rate_hz=rate, arrival_span_s=trace[-1].t_arrival, terms=terms,
+                    terms_per_s=terms / res.wall_s, requests_per_s=n / res.wall_s,
+                    shares={"work": "proportional to outstanding work", "requests": "proportional to live requests",
+                            None: "fixed 12/30/58%"}[policy], clocks=clocks,
+                    p50_first_half_s=float(np.percentile(lat[:half], 50)) if half else None,
+                    p50_second_half_s=float(np.percentile(lat[half:], 50)) if half else None,
+                    p99_first_half_s=float(np.percentile(lat[:half], 99)) if half else None,
+                    p99_second_half_s=float(np.percentile(lat[half:], 99)) if half else None)
+
+    line = {"metric": "serving time to budget (p50/p99, arrival to result read back)", "impl": "ours",
+            "unit": "s", "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "trace": desc,
+            "share_policy": args.serving_policy}
+    if args.serving_study:
+        sat = leg(args.serving_study, args.serving_rate)
+        capacity = sat["requests_per_s"]
+        line.update(saturated=sat, capacity_requests_per_s=capacity,
+                    capacity_basis="requests completed / wall time of the saturated leg (queue never empty "
+                                   "until the drain, so this slightly understates the capacity)",
+                    at_0_8_capacity=leg(args.serving_study_light, 0.8 * capacity))
+    if args.serving_compare:
+        # the same saturated requests under each SM split between the length classes
+        line["share_policies_saturated"] = {str(p): leg(args.serving_compare, args.serving_rate, policy=p)
+                                            for p in (None, "work", "requests")}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ablation(args):
+    """The paper's two control-parameter studies (Tables "alpha" and "par": L=65535, 30 runs
+    of 10^10 sequence evaluations each) at a scale that fits a few GPU-minutes."""
+    import torch
+
+    import paper_2107_09801_gb300 as P
+    from paper_2107_09801_gb300.ablation import alpha_pairs, ls_flip_grid, moves_for_nse
+
+    torch.cuda.set_device(0)
+    L = args.ablation_L
+    line = {"metric": "mean best PSL of independent runs (lower is better)", "impl": "ours", "unit": "PSL",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic (uniform random +-1 starts, run r has seed r)",
+            "L": L, "n_lmt": W.N_LMT}
+    walks = max(3 * args.ablation_runs, 25 * args.grid_runs)
+    with P.Context(arena_bytes=int(walks * P.psl_walk_bytes(L, W.N_LMT, 0) * 1.2) + (64 << 20),
+                   max_walks=walks, steps_per_graph=64) as ctx:
+        t = time.perf_counter()
+        res = alpha_pairs(ctx, L, args.ablation_runs, int(args.ablation_nse))
+        line["alpha_pairs"] = {"runs": args.ablation_runs, "nse_per_run": args.ablation_nse,
+                               "moves_per_run": moves_for_nse(args.ablation_nse, L), "ls_lmt": 2000, "flip_lmt": 10,
+                               "wall_s": time.perf_counter() - t,
+                               "mean_psl": {f"{r.setting.alpha1}/{r.setting.alpha2}": r.mean for r in res},
+                               "std_psl": {f"{r.setting.alpha1}/{r.setting.alpha2}": r.std for r in res},
+                               "psl": {f"{r.setting.alpha1}/{r.setting.alpha2}": r.psl_best for r in res}}
+        t = time.perf_counter()
+        res = ls_flip_grid(ctx, L, args.grid_runs, int(args.grid_nse))
+        line["ls_flip_grid"] = {"runs": args.grid_runs, "nse_per_run": args.grid_nse,
+                                "moves_per_run": moves_for_nse(args.grid_nse, L), "alpha": "4/13",
+                                "wall_s": time.perf_counter() - t,
+                                "mean_psl": {f"LS{r.setting.ls_lmt}/FLIP{r.setting.flip_lmt}": r.mean for r in res}}
+    line["paper_context"] = {"scale": "L=65535, 30 runs, 10^10 NSE per run (A100)",
+                             "alpha_table_mean_psl": {"4/13": 212.700, "4/4": 232.833, "13/13": 238.967}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.ablation:
+        return run_ablation(args)
+    if args.serving_study or args.serving_compare:
+        return run_serving_study(args)
     return run_ours(args)
 
 

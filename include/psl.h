@@ -223,6 +223,24 @@ PSL_API int psl_autotune(psl_ctx *ctx, int reps);
  * choice cached from an earlier psl_autotune).  PSL_EINVAL for unsupported values. */
 PSL_API int psl_set_hot_config(psl_ctx *ctx, int32_t threads, int32_t tile_sb);
 
+/* The lowest fitness F over every pivot the walk has visited (its start, each move, each
+ * perturbed pivot of a phase switch; the first one on ties) and that pivot.  It is kept
+ * when both phases use the same exponent (alpha1 == alpha2), so the objective never
+ * changes; with alpha = 2 it is the energy E = sum_{k>=1} C_k^2, and L^2 / (2E) is the
+ * merit factor defined in Sec. 2.  value_limbs receives 12 little-endian 32-bit limbs of
+ * the exact non-negative integer, value its correctly rounded double, seq_pm1 the
+ * sequence as +1/-1 bytes (cap >= L); each may be NULL.  PSL_ESTATE when alpha1 !=
+ * alpha2, PSL_EBUSY while the walk is queued, PSL_ENOENT for an unknown id. */
+PSL_API int psl_best_fitness(psl_ctx *ctx, int64_t id, uint32_t *value_limbs, double *value, int8_t *seq_pm1,
+                             size_t cap);
+
+/* Resizes the persistent kernels of the context for max_sms SMs (0 = all SMs of the
+ * device; larger values are clamped to the device).  Takes effect at the next psl_step;
+ * results do not change, only which SMs share the work.  Several contexts on one device
+ * whose shares add up to at most the SM count run their steps side by side.  Returns the
+ * SM count now in use, or PSL_EINVAL for a null ctx or max_sms < 0. */
+PSL_API int psl_set_max_sms(psl_ctx *ctx, int32_t max_sms);
+
 /* No counterpart in the paper.  For callers that must not allocate device memory
  * themselves -- code running under another framework's allocator, where a raw cudaFree
  * would synchronise the whole device, or services that reserve every buffer at start-up

@@ -65,7 +65,8 @@ assert TRACE_DTYPE.itemsize == 128  # psl_trace_rec has no implicit padding
 EXPORTED = ["psl_config_default", "psl_init", "psl_submit", "psl_submit_ex", "psl_step", "psl_poll", "psl_best",
             "psl_release", "psl_export_state", "psl_trace", "psl_autocorr", "psl_walk_bytes", "psl_shutdown",
             "psl_last_error", "psl_profile", "psl_profile_read", "psl_autotune", "psl_set_hot_config",
-            "psl_autocorr_static", "psl_inject_stall"]
+            "psl_autocorr_static", "psl_inject_stall", "psl_set_max_sms",
+            "psl_best_fitness"]
 
 _lib = None
 
@@ -104,6 +105,8 @@ def lib():
             "psl_set_hot_config": (ct.c_int, [P, ct.c_int32, ct.c_int32]),
             "psl_autocorr_static": (ct.c_int, [P, ct.c_uint32, P, P]),
             "psl_inject_stall": (ct.c_int, [P, ct.c_int64]),
+            "psl_set_max_sms": (ct.c_int, [P, ct.c_int32]),
+            "psl_best_fitness": (ct.c_int, [P, ct.c_int64, P, P, P, ct.c_size_t]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -343,6 +346,20 @@ class Context:
 
     def _set_hot(self, threads: int, tile_sb: int) -> None:
         psl_set_hot_config(self.h, threads, tile_sb)
+
+    def best_fitness(self, wid: int):
+        """(exact lowest F over the visited pivots, its sequence as +-1 int8) of a walk whose
+        phases share one exponent; with alpha = 2, F is the merit-factor energy."""
+        L = self.L_of[wid]
+        limbs = (ct.c_uint32 * 12)()
+        seq = np.zeros(L, dtype=np.int8)
+        _check(self.h, lib().psl_best_fitness(self.h, wid, ct.addressof(limbs), None, seq.ctypes.data, L))
+        return sum(int(v) << (32 * i) for i, v in enumerate(limbs)), seq
+
+    def set_max_sms(self, max_sms: int) -> int:
+        """Sizes the persistent kernels for max_sms SMs from the next step on (0 = all);
+        returns the SM count in use."""
+        return _check(self.h, lib().psl_set_max_sms(self.h, max_sms))
 
     def inject_stall(self, wid: int) -> None:
         """Test hook: the walk's next neighbourhood pass runs out its bounded waits."""

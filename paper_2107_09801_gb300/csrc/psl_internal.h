@@ -51,7 +51,9 @@ struct WalkDev {
   uint32_t alpha1, alpha2, ls_lmt, topk;
   uint64_t seed, budget;
   uint32_t nchunk_apply, nchunk_rc, trace_cap, has_init_seq;
+  uint32_t track_fbest, pad_static;  // keep the lowest-F pivot (alpha1 == alpha2: one objective)
   uint32_t *bits, *bits_local, *bits_best;  // logical word 0 (guards before and after)
+  uint32_t *bits_fbest;                     // lowest-F pivot (when track_fbest)
   int32_t *C, *C_local;
   float4 *T;          // per k: (Tp4, Tm4, Tp2, Tm2), scaled by 2^(-alpha*e)
   float *score;       // FP32 filter score of window position i at [i-1]
@@ -84,6 +86,7 @@ struct WalkDev {
   float score_min, bound;
   uint32_t flips[kMaxFlips];
   uint32_t F[kWideLimbs], value_local[kWideLimbs], value_step[kWideLimbs];
+  uint32_t F_best[kWideLimbs];  // exact F of bits_fbest
 };
 
 // One unit of the neighbourhood kernel: a block of consecutive window positions.

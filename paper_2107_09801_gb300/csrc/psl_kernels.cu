@@ -36,6 +36,7 @@ __global__ void k_init_bits(WalkDev *hdr, const uint32_t *active) {
     W.bits[idx] = 0u;
     W.bits_local[idx] = 0u;
     W.bits_best[idx] = 0u;
+    if (W.track_fbest) W.bits_fbest[idx] = 0u;
     return;
   }
   if (!W.has_init_seq) {
@@ -128,7 +129,7 @@ __device__ __forceinline__ void apply_one(WalkDev &W, uint32_t chunk) {
   __shared__ int s_max[8];
   __shared__ float s_sum[8];
   __shared__ uint32_t s_F[256 / 32][kWideLimbs];
-  __shared__ uint32_t s_last;
+  __shared__ uint32_t s_last, s_fcopy;
   if (W.status != kRunning) return;
   if (chunk >= W.nchunk_apply) return;
   const int L = (int)W.L;
@@ -308,6 +309,16 @@ __device__ __forceinline__ void apply_one(WalkDev &W, uint32_t chunk) {
       wide_store(W.F, Fs);
       wide_store(W.value_local, Fs);
     }
+    // lowest-F pivot: the start, or a perturbed pivot of a switch below it
+    s_fcopy = 0;
+    if (W.track_fbest && need_F) {
+      uint32_t fb[kWideLimbs];
+      wide_load(fb, W.F_best);
+      if (mode == kModeInit || wide_cmp(Fs, fb) < 0) {
+        wide_store(W.F_best, Fs);
+        s_fcopy = 1;
+      }
+    }
     if (mode == kModeInit) {
       W.psl_best = m;
       W.psl_local = m;
@@ -323,6 +334,11 @@ __device__ __forceinline__ void apply_one(WalkDev &W, uint32_t chunk) {
       W.start = (uint32_t)(splitmix64(W.seed, W.rng_ctr++) % (uint64_t)W.L);
     }
     W.arrive = 0;
+  }
+  if (W.track_fbest && need_F) {  // the same branch for every thread of the block
+    __syncthreads();
+    if (s_fcopy)
+      for (int w = threadIdx.x; w < nw; w += blockDim.x) W.bits_fbest[w] = W.bits[w];
   }
 }
 
@@ -645,13 +661,29 @@ __device__ __forceinline__ void decide_one(WalkDev &W) {
   // psl_best / solution_best: the first neighbour reaching the window minimum
   const bool psl_imp = W.ktau_on && W.win_psl < W.psl_best;
   const uint32_t pj = (uint32_t)(((uint64_t)W.start + W.win_psl_i) % (uint64_t)L);
-  if (psl_imp) {
+  // lowest-F pivot (one objective): the move's result when it is below every earlier pivot
+  bool f_imp = false;
+  if (W.track_fbest) {
+    uint32_t v[kWideLimbs], fb[kWideLimbs];
+    wide_load(v, s_best);
+    wide_load(fb, W.F_best);
+    f_imp = wide_cmp(v, fb) < 0;
+  }
+  if (psl_imp || f_imp) {
     const int nw = (int)W.nw;
-    for (int w = threadIdx.x; w < nw; w += blockDim.x) W.bits_best[w] = W.bits[w];
+    for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+      const uint32_t b = W.bits[w];
+      if (psl_imp) W.bits_best[w] = b;
+      if (f_imp) W.bits_fbest[w] = b;
+    }
     __syncthreads();
-    if (threadIdx.x == 0) W.bits_best[pj >> 5] ^= 1u << (pj & 31);
+    if (threadIdx.x == 0) {
+      if (psl_imp) W.bits_best[pj >> 5] ^= 1u << (pj & 31);
+      if (f_imp) W.bits_fbest[kstar >> 5] ^= 1u << (kstar & 31);
+    }
   }
   if (threadIdx.x != 0) return;
+  if (f_imp) wide_store(W.F_best, s_best);
 
   const int32_t e_used = W.e;  // scale of this step's tables, before the next one is chosen
   uint32_t vstep[kWideLimbs], vlocal[kWideLimbs];

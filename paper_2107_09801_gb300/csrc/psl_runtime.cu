@@ -34,7 +34,7 @@ double now_s() {
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-  size_t bits, bits_local, bits_best, C, C_local, T, score, score_part, pslj, ktau, cand, rc_part, ap_part, trace, total;
+  size_t bits, bits_local, bits_best, bits_fbest, C, C_local, T, score, score_part, pslj, ktau, cand, rc_part, ap_part, trace, total;
 };
 
 Layout layout_for(uint32_t L, uint32_t N, uint32_t trace_cap) {
@@ -52,6 +52,7 @@ Layout layout_for(uint32_t L, uint32_t N, uint32_t trace_cap) {
   o.bits = take(words * 4);
   o.bits_local = take(words * 4);
   o.bits_best = take(words * 4);
+  o.bits_fbest = take(words * 4);
   o.C = take((size_t)L * 4);
   o.C_local = take((size_t)L * 4);
   o.T = take((size_t)L * 16);
@@ -143,7 +144,8 @@ struct psl_ctx {
   bool active_dirty = true;
   uint32_t nitems = 0, max_chunk_apply = 1, max_chunk_rc = 1;
   int64_t next_id = 0;
-  uint32_t sm_count = 152;
+  uint32_t sm_count = 152;   // SMs the persistent kernels are sized for
+  uint32_t dev_sms = 152;    // SMs of the device
   std::string err;
   // CUDA graph of steps_per_graph steps over the current active set
   cudaGraphExec_t graph = nullptr;
@@ -313,7 +315,7 @@ extern "C" int psl_init(const psl_config *cfg_in, psl_ctx **out) {
   {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, cfg.device) == cudaSuccess && sms > 0)
-      ctx->sm_count = (uint32_t)sms;
+      ctx->sm_count = ctx->dev_sms = (uint32_t)sms;
     if (cfg.max_sms > 0) ctx->sm_count = std::min<uint32_t>(ctx->sm_count, (uint32_t)cfg.max_sms);
   }
   if (prepare_kernels() != cudaSuccess) {
@@ -437,6 +439,8 @@ static void fill_header(psl_ctx *ctx, HostWalk &w, WalkDev &h) {
   h.bits = (uint32_t *)(base + w.lay.bits) + kGuardWords;
   h.bits_local = (uint32_t *)(base + w.lay.bits_local) + kGuardWords;
   h.bits_best = (uint32_t *)(base + w.lay.bits_best) + kGuardWords;
+  h.bits_fbest = (uint32_t *)(base + w.lay.bits_fbest) + kGuardWords;
+  h.track_fbest = p.alpha1 == p.alpha2 ? 1u : 0u;
   h.C = (int32_t *)(base + w.lay.C);
   h.C_local = (int32_t *)(base + w.lay.C_local);
   h.T = (float4 *)(base + w.lay.T);
@@ -904,6 +908,21 @@ extern "C" int psl_best(psl_ctx *ctx, int64_t id, int32_t *psl_out, int8_t *seq,
   return PSL_OK;
 }
 
+extern "C" int psl_best_fitness(psl_ctx *ctx, int64_t id, uint32_t *value_limbs, double *value, int8_t *seq,
+                                size_t cap) {
+  if (!ctx) return PSL_EINVAL;
+  HostWalk *w = find(ctx, id);
+  if (!w) return PSL_ENOENT;
+  if (w->slot < 0) return PSL_EBUSY;
+  if (w->p.alpha1 != w->p.alpha2) return fail(ctx, PSL_ESTATE, "alpha1 != alpha2: F of the two phases differ");
+  if (seq && cap < w->p.L) return fail(ctx, PSL_EINVAL, "cap %zu < L %u", cap, w->p.L);
+  const WalkDev &h = ctx->h_hdr[w->slot];
+  if (value_limbs) std::memcpy(value_limbs, h.F_best, sizeof h.F_best);
+  if (value) *value = limbs_to_double(h.F_best);
+  if (seq) return download_pm1(ctx, h.bits_fbest, w->p.L, seq);
+  return PSL_OK;
+}
+
 extern "C" int psl_release(psl_ctx *ctx, int64_t id) {
   if (!ctx) return PSL_EINVAL;
   HostWalk *w = find(ctx, id);
@@ -1088,6 +1107,20 @@ extern "C" int psl_set_hot_config(psl_ctx *ctx, int32_t threads, int32_t tile_sb
     ctx->graph = nullptr;
   }
   return PSL_OK;
+}
+
+extern "C" int psl_set_max_sms(psl_ctx *ctx, int32_t max_sms) {
+  if (!ctx || max_sms < 0) return PSL_EINVAL;
+  const uint32_t n = max_sms == 0 ? ctx->dev_sms : std::min<uint32_t>(ctx->dev_sms, (uint32_t)max_sms);
+  if (n == ctx->sm_count) return (int)n;
+  ctx->sm_count = n;
+  ctx->cfg.max_sms = max_sms;
+  ctx->active_dirty = true;  // the k split of each walk depends on the SM count
+  if (ctx->graph) {          // captured with the old grid sizes
+    cudaGraphExecDestroy(ctx->graph);
+    ctx->graph = nullptr;
+  }
+  return (int)n;
 }
 
 extern "C" int psl_inject_stall(psl_ctx *ctx, int64_t id) {

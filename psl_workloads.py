@@ -76,6 +76,14 @@ def batch_1048575(walks: int = 148, budget: int = 200) -> Workload:
                     "L=1048575, seeds 0..walks-1, alpha 4/10, N_lmt 6912, 200 moves")
 
 
+def labs_1023(walks: int = 4096, budget: int = 2000) -> Workload:
+    """The merit-factor objective: alpha = 2 in both phases, so F is the energy sum C_k^2
+    and MF = L^2 / (2 F); the full neighbourhood (N = L)."""
+    return Workload(f"LABS_L1023_x{walks}",
+                    tuple(WalkSpec(L=1023, seed=s, alpha1=2, alpha2=2, budget=budget) for s in range(walks)),
+                    "L=1023, seeds 0..walks-1, alpha 2/2 (energy of the merit factor), N = L, LS_lmt 2000")
+
+
 @dataclass(frozen=True)
 class Request:
     t_arrival: float

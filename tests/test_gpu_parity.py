@@ -145,6 +145,25 @@ def test_batch_composition_invariance(P):
         assert np.array_equal(st["C"], st1["C"]) and np.array_equal(st["pivot"], st1["pivot"])
 
 
+def test_resizing_sm_share_mid_run_keeps_results(P):
+    """The SM count a context's kernels are sized for changes which blocks score which k
+    range, never a decision: resize between steps and compare with the oracle."""
+    specs = W.small_specs(seed=21, count=6, L_choices=(255, 1023, 4095)) + [W.WalkSpec(L=40000, seed=9, budget=6,
+                                                                                          ls_lmt=4)]
+    with P.Context(arena_bytes=ARENA, max_walks=16, steps_per_graph=4) as ctx:
+        ids = [submit_spec(ctx, s) for s in specs]
+        for sms in (7, 0, 33, 152, 1, 0):
+            assert ctx.set_max_sms(sms) >= 1
+            ctx.step(3)
+        ctx.run()
+        for i, s in zip(ids, specs):
+            w = oracle_walk(s)
+            compare_traces(ctx.trace(i, s.budget), w.run(s.budget), f"L={s.L}")
+            compare_final_state(ctx.export_state(i), w)
+        with pytest.raises(P.PslError):
+            ctx.set_max_sms(-1)
+
+
 def test_continuous_admission_matches_alone(P):
     """Walks submitted while others are on the GPU, admitted as memory frees up."""
     specs = [W.WalkSpec(L=L, seed=100 + r, alpha1=2 + r % 4, alpha2=9 + r % 5, budget=20 + 7 * r, ls_lmt=5)
@@ -388,3 +407,65 @@ def test_restart_rounds_match_oracle(P):
         assert hist[r].psl_best == found[i_best][0] and hist[r].walk == i_best
         assert np.array_equal(hist[r].sequence, start)
     assert hist[-1].psl_best <= hist[0].psl_best
+
+
+# ------------------------------------------------------------------------------------------------
+# control-parameter studies (alpha pairs, LS_lmt x FLIP_lmt) at a tiny scale: every run's best
+# PSL and best sequence equal the oracle's walk with the same parameters
+# ------------------------------------------------------------------------------------------------
+def test_parameter_studies_match_oracle(P):
+    from paper_2107_09801_gb300.ablation import alpha_pairs, ls_flip_grid, moves_for_nse
+    L, runs, nse = 255, 2, 255 * 24
+    with P.Context(arena_bytes=ARENA, max_walks=64, steps_per_graph=4) as ctx:
+        res = alpha_pairs(ctx, L, runs, nse, ls_lmt=4, flip_lmt=3) + \
+            ls_flip_grid(ctx, L, runs, nse, ls_values=(8, 2), flip_values=(5, 1), seed0=40)
+    budget = moves_for_nse(nse, L)
+    assert budget == 24 and len(res) == 3 + 4
+    for i, r in enumerate(res):
+        st = r.setting
+        seed0 = 0 if i < 3 else 40
+        for k, got in enumerate(r.psl_best):
+            w = oracle_walk(W.WalkSpec(L=L, seed=seed0 + k, alpha1=st.alpha1, alpha2=st.alpha2, budget=budget,
+                                       ls_lmt=st.ls_lmt, flip_lmt=st.flip_lmt))
+            w.run(budget)
+            assert got == w.psl_best, (st, k)
+
+
+# ------------------------------------------------------------------------------------------------
+# one objective (alpha1 == alpha2): the lowest-F pivot; alpha = 2 is the merit-factor energy
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("form", ["batched", "plain"])
+def test_lowest_fitness_pivot_matches_oracle(P, form):
+    specs = [W.WalkSpec(L=L, seed=70 + r, alpha1=a, alpha2=a, budget=b, ls_lmt=ls, flip_lmt=5)
+             for r, (L, a, b, ls) in enumerate([(31, 2, 60, 3), (255, 2, 50, 4), (1023, 2, 30, 1000),
+                                                 (4095, 3, 12, 2), (127, 5, 40, 5), (2000, 2, 16, 3)])]
+    other = W.WalkSpec(L=255, seed=5, alpha1=2, alpha2=4, budget=10)
+    with P.Context(form=form, arena_bytes=ARENA, max_walks=16, steps_per_graph=4) as ctx:
+        ids = [submit_spec(ctx, s) for s in specs]
+        oid = submit_spec(ctx, other)
+        ctx.run()
+        for i, s in zip(ids, specs):
+            w = oracle_walk(s)
+            compare_traces(ctx.trace(i, s.budget), w.run(s.budget), f"L={s.L}")
+            F_best, seq = ctx.best_fitness(i)
+            assert F_best == w.F_best, (s, F_best, w.F_best)
+            assert np.array_equal(seq, w.fbest_seq), s
+        with pytest.raises(P.PslError):
+            ctx.best_fitness(oid)
+
+
+def test_merit_factor_workload_sampled_walks(P):
+    """The alpha = 2 workload at full size (L=1023, full neighbourhood, 4096 walks): every
+    walk's lowest energy equals sum C_k^2 of its sequence, and sampled walks follow the oracle."""
+    specs = W.labs_1023(4096, budget=12).walks
+    with P.Context(arena_bytes=ARENA, max_walks=len(specs), steps_per_graph=4) as ctx:
+        ids = [submit_spec(ctx, s, trace=False) for s in specs]
+        ctx.run()
+        got = [ctx.best_fitness(i) for i in ids]
+        for E, seq in got[::97]:
+            c = np.correlate(seq.astype(np.int64), seq.astype(np.int64), "full")[len(seq):]
+            assert E == int(np.dot(c, c))
+        for r in (0, 1, 2047, 4095):
+            w = oracle_walk(specs[r])
+            w.run(specs[r].budget)
+            assert got[r][0] == w.F_best and np.array_equal(got[r][1], w.fbest_seq), r
