@@ -155,6 +155,16 @@ class OracleSampler:
         O.eval_neighbours(w0.s, w0.C, alpha, [1, 2])
         self.per = max((time.perf_counter() - t0) / 2, 1e-5)
 
+    def sample_one_core(self, seconds: float):
+        """The same work on one host thread (the paper's CPU solver ran on one core)."""
+        n_per = int(max(1, min(self.n_lmt, seconds / self.per)))
+        w = self.walks[0]
+        start = self.O.splitmix64(w.p.seed, w.rng_ctr) % self.L
+        t0 = time.perf_counter()
+        self.O.eval_neighbours(w.s, w.C, self.alpha, [(start + i) % self.L for i in range(1, n_per + 1)])
+        dt = time.perf_counter() - t0
+        return n_per / dt, n_per, dt
+
     def sample(self, seconds: float):
         n_per = int(max(1, min(self.n_lmt, seconds / self.per)))
 
@@ -474,9 +484,12 @@ def run_ours(args):
             sampler = OracleSampler(L, N, 4)
             v, n_per, dt = sampler.sample(args.cpu_sample_s)
             cores = sampler.threads
+            v1, n1, dt1 = sampler.sample_one_core(min(3.0, args.cpu_sample_s))
             line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
                                     "sample": f"{cores} threads x {n_per} window neighbours of their own L=131071 "
-                                              f"walk, exact F and PSL each ({dt:.1f} s)"}
+                                              f"walk, exact F and PSL each ({dt:.1f} s)",
+                                    "one_core": {"value": v1, "unit": UNIT, "sample": f"1 thread x {n1} window "
+                                                 f"neighbours ({dt1:.1f} s)"}}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

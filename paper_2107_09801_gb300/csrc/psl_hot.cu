@@ -88,8 +88,11 @@ __device__ __forceinline__ uint32_t window32_ro(const uint32_t *__restrict__ bit
 }
 
 // tables of group q of super-block sb of the tile (first k of the group: kg)
-// (the tile's per-k values come from the shared staging buffer Ts, entry kg - kt0)
-__device__ __forceinline__ void build_group(float *tab, int sb, int q, const float4 *Ts, int kt0, int kg, int L) {
+// (the tile's per-k values come from the shared staging buffer Ts, entry kg - kt0).
+// W1/W0 are built only when some lane of the block scores a two-partner shift in the
+// super-block (need_w), E only when some lane scores a one-partner shift there (need_e).
+__device__ __forceinline__ void build_group(float *tab, int sb, int q, const float4 *Ts, int kt0, int kg, int L,
+                                            bool need_w, bool need_e) {
   float tp4[5], tm4[5], tp2[5], tm2[5];
 #pragma unroll
   for (int t = 0; t < 5; t++) {
@@ -122,40 +125,50 @@ __device__ __forceinline__ void build_group(float *tab, int sb, int q, const flo
   }
   float *base = tab + sb * kSbFloats + q * 96;
   const int sw = sb & 31;
+  if (need_w) {
 #pragma unroll
-  for (int b = 0; b < 32; b++) {
-    const int lo = b & 3, hi = b >> 2;
-    base[b ^ sw] = lo == 0 ? hi1[hi] : (hi == 0 ? lo1[lo] : lo1[lo] + hi1[hi]);
-    base[32 + (b ^ sw)] = lo == 0 ? hi0[hi] : (hi == 0 ? lo0[lo] : lo0[lo] + hi0[hi]);
-    base[64 + (b ^ sw)] = loe[lo] + hie[hi];
+    for (int b = 0; b < 32; b++) {
+      const int lo = b & 3, hi = b >> 2;
+      base[b ^ sw] = lo == 0 ? hi1[hi] : (hi == 0 ? lo1[lo] : lo1[lo] + hi1[hi]);
+      base[32 + (b ^ sw)] = lo == 0 ? hi0[hi] : (hi == 0 ? lo0[lo] : lo0[lo] + hi0[hi]);
+    }
+  }
+  if (need_e) {
+#pragma unroll
+    for (int b = 0; b < 32; b++) base[64 + (b ^ sw)] = loe[b & 3] + hie[b >> 2];
   }
 }
 
-// exact per-term contribution used where a group straddles a region boundary
-__device__ __forceinline__ float term_slow(const float4 *__restrict__ T, int k, int kin, int kout, uint32_t U,
-                                           uint32_t V, bool plus_side, int t) {
-  if (k > kout) return 0.f;
-  const float4 tv = __ldg(T + k);
-  const uint32_t u = (U >> t) & 1u, v = (V >> t) & 1u;
-  if (k <= kin) return (u & v) ? tv.x : ((u | v) ? 0.f : tv.y);
-  const uint32_t e = plus_side ? u : v;
-  return e ? tv.z : tv.w;
-}
+// Shift range of one warp's lanes: min/max of kin and kout over its 32 neighbours.
+struct WarpRange {
+  int kin_lo, kin_hi, kout_lo, kout_hi;
+};
 
-// one group of a super-block where lanes may sit in different regions
+// One group of a super-block where lanes may sit in different regions.  The choice is
+// warp-uniform: a table lookup when every lane of the warp has both partners (or every
+// lane exactly one) for all five shifts; otherwise the five terms one by one from the
+// tile's staged per-k values, each lane selecting its own case without a branch.
 template <int Q>
 __device__ __forceinline__ void group_generic(float &a0, float &a1, uint32_t bsw, uint32_t W1, uint32_t W0,
                                               uint32_t E, uint32_t U, uint32_t V, int ka, int kin, int kout,
-                                              bool plus_side, const float4 *__restrict__ T) {
+                                              bool plus_side, const float4 *Ts, int kt0, const WarpRange &wr) {
   const int kg = ka + 5 * Q;
-  if (kg + 4 <= kin) {
+  if (kg > wr.kout_hi) return;
+  if (kg + 4 <= wr.kin_lo) {
     a0 += lds_at<Q * 384>(field4<Q>(W1) ^ bsw);
     a1 += lds_at<Q * 384 + 128>(field4<Q>(W0) ^ bsw);
-  } else if (kg > kin && kg + 4 <= kout) {
+  } else if (kg > wr.kin_hi && kg + 4 <= wr.kout_lo) {
     a0 += lds_at<Q * 384 + 256>(field4<Q>(E) ^ bsw);
-  } else if (kg <= kout) {
+  } else {
 #pragma unroll
-    for (int t = 0; t < 5; t++) a1 += term_slow(T, kg + t, kin, kout, U, V, plus_side, 5 * Q + t);
+    for (int t = 0; t < 5; t++) {
+      const int k = kg + t;
+      const float4 tv = Ts[k - kt0];
+      const uint32_t u = (U >> (5 * Q + t)) & 1u, v = (V >> (5 * Q + t)) & 1u;
+      const float r_in = (u & v) ? tv.x : ((u | v) ? 0.f : tv.y);  // both partners
+      const float r_ed = (plus_side ? u : v) ? tv.z : tv.w;        // one partner
+      a1 += k <= kin ? r_in : (k <= kout ? r_ed : 0.f);
+    }
   }
 }
 
@@ -208,20 +221,23 @@ __device__ __forceinline__ void sb_edge(float &a0, float &a1, const uint32_t *__
   a1 += lds_at<5 * 384 + 256>(field4<5>(E) ^ bsw);
 }
 
-// One super-block where region boundaries fall inside it for some lane.
+// One super-block where region boundaries fall inside it for some lane of the warp.
+// Partner bits outside the sequence (clamped windows) are only ever paired with a case
+// that ignores them.
 __device__ __forceinline__ void sb_generic(float &a0, float &a1, const uint32_t *__restrict__ bits,
-                                           const float4 *__restrict__ T, int j, int ka, int kin, int kout,
-                                           bool plus_side, uint32_t M, uint32_t bsw, int cap_u) {
-  if (ka > kout) return;
+                                           const float4 *Ts, int kt0, int j, int ka, int kin, int kout,
+                                           bool plus_side, uint32_t M, uint32_t bsw, int cap_u,
+                                           const WarpRange &wr) {
+  if (ka > wr.kout_hi) return;
   const uint32_t U = window32_ro(bits, min(j + ka, cap_u)) ^ M;
   const uint32_t V = __brev(window32_ro(bits, max(j - ka - 31, -64))) ^ M;
   const uint32_t W1 = U & V, W0 = ~(U | V), E = plus_side ? U : V;
-  group_generic<0>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-  group_generic<1>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-  group_generic<2>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-  group_generic<3>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-  group_generic<4>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
-  group_generic<5>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, T);
+  group_generic<0>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
+  group_generic<1>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
+  group_generic<2>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
+  group_generic<3>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
+  group_generic<4>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
+  group_generic<5>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
 }
 
 __device__ __forceinline__ void flush2(float &hi, float &lo, float &a0, float &a1) {
@@ -236,13 +252,43 @@ __device__ __forceinline__ int sb_count(int bound, int kt0, int off, int nsb) {
   return d < 0 ? 0 : min(nsb, d / kSbK + 1);
 }
 
-// Scores one work item (a block of window positions, possibly one k-chunk of them).
-// Returns false when a staged copy timed out: the block must then stop taking work.
+// TMA bulk copy of the per-k values T[kt0 .. kt0 + kTileK) (those below L) into staging
+// buffer q & 1, signalling that buffer's mbarrier; q counts the block's copies.
+template <int NSB>
+__device__ __forceinline__ void stage_copy(uint32_t stage_s, uint32_t mbar_s, uint32_t q, const float4 *T, int kt0,
+                                           int L) {
+  constexpr int kTileK = NSB * kSbK;
+  const uint32_t bytes = 16u * (uint32_t)min(kTileK, L - kt0);
+  const uint32_t mb = mbar_s + 8u * (q & 1u);
+  fence_proxy_async();
+  mbar_expect_tx(mb, bytes);
+  tma_load_1d(stage_s + (q & 1u) * (uint32_t)(kTileK * 16), T + kt0, bytes, mb);
+}
+
+// first shift of the k range a work item scores (its k-chunk, or the whole range)
+template <int NSB>
+__device__ __forceinline__ int item_tile_lo(const WalkDev &W, const HotItem &it) {
+  return W.ksplit > 1 ? (int)it.kc * ((int)W.kchunk_sb / NSB) : 0;
+}
+
+// Copies a block has staged: copy q goes to buffer q & 1 and completes phase q >> 1 of that
+// buffer's mbarrier, so it is awaited with parity (q >> 1) & 1.  `seq` is the next copy the
+// block will consume; `pre` says that copy was already issued for the current item's first
+// tile while the previous item scored its last one.
+struct HotPipe {
+  uint32_t seq;
+  bool pre;
+};
+
+// Scores one work item (a block of window positions, possibly one k-chunk of them).  At the
+// start of its last tile thread 0 takes the next item from the schedule and, when that
+// item's walk is running, issues the copy of its first tile, so the copy overlaps this
+// tile.  Returns false when a staged copy timed out: the block must then stop taking work.
 template <int NT, int NSB>
-__device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem it) {
+__device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem *items, Schedule *sched, const uint32_t item,
+                                        HotPipe &pipe, uint32_t mbar_s, uint32_t *s_next) {
   static_assert(NSB <= 32, "the per-super-block swizzle assumes at most 32 super-blocks per tile");
   extern __shared__ __align__(128) float smem_raw[];
-  __shared__ __align__(8) uint64_t s_mbar[2];
   const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(smem_raw);
   const uint32_t tab_s = (raw_s + 127u) & ~127u;  // lookups OR a swizzle into the low 7 bits
   float *tab = smem_raw + (tab_s - raw_s) / 4;
@@ -251,9 +297,51 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem it) {
   const uint32_t stage_s = tab_s + NSB * kSbBytes;
   int *s_kmax = reinterpret_cast<int *>(stage + 2 * kTileK);
   int *s_timeout = s_kmax + 1;
-  const uint32_t mbar_s = (uint32_t)__cvta_generic_to_shared(s_mbar);
+  int *s_kin_lo = s_kmax + 2, *s_kin_hi = s_kmax + 3;  // block-wide range of kin
+  int *s_run = s_kmax + 4;                              // the walk was running when the item began
+  int *s_pre = s_kmax + 5;                              // the next item's first copy is issued
+  const HotItem it = items[item];
   WalkDev &W = hdr[it.slot];
-  if (W.status != kRunning) return true;
+  // thread 0 takes the next item (copy q issued for its first tile when `prefetch`)
+  auto take_next = [&](bool prefetch, uint32_t q) {
+    const uint32_t nx = atomicAdd(&sched->hot_next, 1u);
+    *s_next = nx;
+    *s_pre = 0;
+    if (prefetch && nx < sched->nitems) {
+      const HotItem in = items[nx];
+      const WalkDev &Wn = hdr[in.slot];
+      const int kt0n = 1 + item_tile_lo<NSB>(Wn, in) * kTileK;
+      if (Wn.status == kRunning && !Wn.inject_stall && kt0n < (int)Wn.L) {
+        stage_copy<NSB>(stage_s, mbar_s, q, Wn.T, kt0n, (int)Wn.L);
+        *s_pre = 1;
+      }
+    }
+  };
+  // every thread waits on copy q (bounded)
+  auto wait_copy = [&](uint32_t q, int limit) {
+    return mbar_wait_bounded(mbar_s + 8u * (q & 1u), (q >> 1) & 1u, limit);
+  };
+  if (threadIdx.x == 0) {
+    *s_kmax = 0;
+    *s_timeout = 0;
+    *s_kin_lo = INT_MAX;
+    *s_kin_hi = 0;
+    *s_run = W.status == kRunning ? 1 : 0;  // one reading for the whole block
+  }
+  __syncthreads();
+  if (!*s_run) {
+    // a copy issued for this item is consumed before its buffer is used again
+    if (pipe.pre) {
+      if (!wait_copy(pipe.seq, 1 << 20)) *s_timeout = 1;
+      pipe.seq++;
+    }
+    __syncthreads();
+    if (*s_timeout) return false;  // the copy may still be in flight: stop using this block
+    if (threadIdx.x == 0) take_next(false, pipe.seq);
+    __syncthreads();
+    pipe.pre = *s_pre != 0;
+    return true;
+  }
   const int L = (int)W.L, N = (int)W.N;
   const uint32_t *__restrict__ bits = W.bits;
   const float4 *__restrict__ T = W.T;
@@ -271,49 +359,62 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem it) {
   const int w_kin_hi = __reduce_max_sync(0xffffffffu, kin);
   const int w_kout_lo = __reduce_min_sync(0xffffffffu, kout);
   const int w_kout_hi = warp_live ? __reduce_max_sync(0xffffffffu, kout) : 0;
-  if (threadIdx.x == 0) {
-    *s_kmax = 0;
-    *s_timeout = 0;
-    mbar_init(mbar_s, 1);
-    mbar_init(mbar_s + 8, 1);
-    fence_mbar_init();
+  const WarpRange wr{w_kin_lo, w_kin_hi, w_kout_lo, w_kout_hi};
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(s_kmax, w_kout_hi);
+    atomicMin(s_kin_lo, w_kin_lo);
+    atomicMax(s_kin_hi, w_kin_hi);
   }
   __syncthreads();
-  if ((threadIdx.x & 31) == 0) atomicMax(s_kmax, w_kout_hi);
-  __syncthreads();
   const int kmax = *s_kmax;
+  const int blk_kin_lo = *s_kin_lo, blk_kin_hi = *s_kin_hi;
   // tiles of this block: all of them, or those of its k-chunk when the k range is split
   const int tiles_per_chunk = (int)W.kchunk_sb / NSB;
-  const int tile_lo = W.ksplit > 1 ? (int)it.kc * tiles_per_chunk : 0;
+  const int tile_lo = item_tile_lo<NSB>(W, it);
   const int tile_hi = W.ksplit > 1 ? min((kmax + kTileK - 1) / kTileK, tile_lo + tiles_per_chunk)
                                    : (kmax + kTileK - 1) / kTileK;
   const int ntiles = max(0, tile_hi - tile_lo);
-  // TMA bulk copy of tile t's per-k values T[kt0 .. kt0 + kTileK) (those below L) into buffer t & 1
-  auto stage_tile = [&](int t) {
-    const int kt0 = 1 + (tile_lo + t) * kTileK;
-    const uint32_t bytes = 16u * (uint32_t)min(kTileK, L - kt0);
-    const uint32_t mb = mbar_s + 8u * (t & 1);
-    fence_proxy_async();
-    mbar_expect_tx(mb, bytes);
-    tma_load_1d(stage_s + (uint32_t)((t & 1) * kTileK * 16), T + kt0, bytes, mb);
-  };
-  // test hook: no copy is issued, so every wait below runs out (short limit) and the walk
-  // is marked failed; nothing is left in flight
+  // test hook: no copy is issued for this walk, so every wait below runs out (short limit)
+  // and the walk is marked failed; nothing of it is left in flight
   const bool stall = W.inject_stall != 0;
   const int wait_limit = stall ? 64 : (1 << 20);
-  if (threadIdx.x == 0 && ntiles > 0 && !stall) stage_tile(0);
+  if (pipe.pre && ntiles == 0) {  // staged for nothing: consume it
+    if (!wait_copy(pipe.seq, 1 << 20)) *s_timeout = 1;
+    pipe.seq++;
+    pipe.pre = false;
+  }
+  if (threadIdx.x == 0 && ntiles > 0 && !stall && !pipe.pre)
+    stage_copy<NSB>(stage_s, mbar_s, pipe.seq, T, 1 + tile_lo * kTileK, L);
+  if (ntiles == 0) {
+    __syncthreads();
+    if (threadIdx.x == 0) take_next(true, pipe.seq);
+  }
 
   float hi = 0.f, lo = 0.f, a0 = 0.f, a1 = 0.f;
   for (int tile = 0; tile < ntiles; tile++) {
     const int kt0 = 1 + (tile_lo + tile) * kTileK;
+    const uint32_t cq = pipe.seq + (uint32_t)tile;  // this tile's copy
     __syncthreads();  // previous tile fully consumed (tables, and the staging buffer reused below)
-    if (threadIdx.x == 0 && tile + 1 < ntiles && !stall) stage_tile(tile + 1);
+    if (threadIdx.x == 0) {
+      if (tile + 1 < ntiles) {
+        if (!stall) stage_copy<NSB>(stage_s, mbar_s, cq + 1, T, kt0 + kTileK, L);
+      } else {
+        take_next(!stall, cq + 1);
+      }
+    }
+    // every thread observes the copy's completion: the builders read the staged values, and
+    // so does the generic path of any warp while it scores this tile
+    if (!wait_copy(cq, wait_limit)) *s_timeout = 1;
     if ((int)threadIdx.x < 6 * NSB) {
-      if (!mbar_wait_bounded(mbar_s + 8u * (tile & 1), (uint32_t)(tile >> 1) & 1u, wait_limit)) *s_timeout = 1;
-      const float4 *Ts = stage + (tile & 1) * kTileK;
+      const float4 *Ts = stage + (cq & 1u) * kTileK;
       for (int t = threadIdx.x; t < 6 * NSB; t += NT) {
         const int sb = t % NSB, q = t / NSB;
-        build_group(tab, sb, q, Ts, kt0, kt0 + sb * kSbK + 5 * q, L);
+        const int ka = kt0 + sb * kSbK;  // first shift of the super-block
+        // two-partner shifts k <= kin exist here for some lane iff ka <= max kin; one-partner
+        // shifts kin < k <= kout iff ka + 29 > min kin and ka <= max kout
+        const bool need_w = ka <= blk_kin_hi;
+        const bool need_e = ka + kSbK - 1 > blk_kin_lo && ka <= kmax;
+        if (need_w || need_e) build_group(tab, sb, q, Ts, kt0, ka + 5 * q, L, need_w, need_e);
       }
     }
     __syncthreads();
@@ -343,8 +444,10 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem it) {
         sb++;
       }
     }
+    const float4 *Ts = stage + (cq & 1u) * kTileK;  // this tile's per-k values, still staged
     for (; sb < e0; sb++) {
-      sb_generic(a0, a1, bits, T, j, kt0 + sb * kSbK, kin, kout, plus_side, M, bsw0 + sb * (kSbBytes + 4), cap_u);
+      sb_generic(a0, a1, bits, Ts, kt0, j, kt0 + sb * kSbK, kin, kout, plus_side, M, bsw0 + sb * (kSbBytes + 4),
+                 cap_u, wr);
       flush2(hi, lo, a0, a1);
     }
     {
@@ -364,22 +467,35 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem it) {
       }
     }
     for (; sb < n_all; sb++) {
-      sb_generic(a0, a1, bits, T, j, kt0 + sb * kSbK, kin, kout, plus_side, M, bsw0 + sb * (kSbBytes + 4), cap_u);
+      sb_generic(a0, a1, bits, Ts, kt0, j, kt0 + sb * kSbK, kin, kout, plus_side, M, bsw0 + sb * (kSbBytes + 4),
+                 cap_u, wr);
       flush2(hi, lo, a0, a1);
     }
   }
+  __syncthreads();  // the next item and its copy flag are visible to every thread
+  const bool next_pre = *s_pre != 0;
   if (*s_timeout) {
     // a staged copy never arrived: give every copy of this block one more bounded wait,
     // then mark the walk failed instead of using its scores
-    __syncthreads();
     if (threadIdx.x == 0) {
-      if (!stall)
-        for (int t = max(0, ntiles - 2); t < ntiles; t++) mbar_wait_bounded(mbar_s + 8u * (t & 1), (uint32_t)(t >> 1) & 1u);
+      if (!stall) {
+        const uint32_t last = pipe.seq + (uint32_t)ntiles + (next_pre ? 1u : 0u);
+        for (uint32_t q = last >= 2 ? last - 2 : 0; q < last; q++) wait_copy(q, 1 << 20);
+        // the item taken for this block will not be scored: its walk fails too
+        if (*s_next < sched->nitems) {
+          WalkDev &Wn = hdr[items[*s_next].slot];
+          Wn.error = (uint32_t)-5;
+          Wn.status = kError;
+        }
+      }
       W.error = (uint32_t)-5;  // PSL_ETIMEOUT of the library header
       W.status = kError;
     }
-    return stall;  // after a real timeout a copy may still be in flight: stop using this block
+    if (!stall) return false;  // a copy may still be in flight: stop using this block
   }
+  if (!stall) pipe.seq += (uint32_t)ntiles;
+  pipe.pre = next_pre;
+  if (*s_timeout) return true;
   if (!live) return true;
   if (W.ksplit > 1) {
     W.score_part[(size_t)it.kc * N + (i - 1)] = hi + lo;
@@ -402,14 +518,22 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem it) {
 // (longest walks first in the item list).
 template <int NT, int NSB>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_hot_batched(WalkDev *hdr, const HotItem *items, Schedule *sched) {
-  __shared__ uint32_t s_item;
+  __shared__ __align__(8) uint64_t s_mbar[2];
+  __shared__ uint32_t s_next;
+  const uint32_t mbar_s = (uint32_t)__cvta_generic_to_shared(s_mbar);
+  if (threadIdx.x == 0) {
+    mbar_init(mbar_s, 1);
+    mbar_init(mbar_s + 8, 1);
+    fence_mbar_init();
+    s_next = atomicAdd(&sched->hot_next, 1u);
+  }
+  __syncthreads();
+  HotPipe pipe{0u, false};
   for (;;) {
-    __syncthreads();  // the previous item's shared memory is free
-    if (threadIdx.x == 0) s_item = atomicAdd(&sched->hot_next, 1u);
-    __syncthreads();
-    const uint32_t item = s_item;
+    const uint32_t item = s_next;
     if (item >= sched->nitems) break;
-    if (!hot_one<NT, NSB>(hdr, items[item])) break;
+    __syncthreads();  // every thread has read the item before it is replaced
+    if (!hot_one<NT, NSB>(hdr, items, sched, item, pipe, mbar_s, &s_next)) break;
   }
 }
 
