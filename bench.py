@@ -15,6 +15,7 @@ Prints one JSON line on rank 0.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import csv
 import hashlib
 import io
@@ -48,6 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--walks", type=int, default=1024)
+    ap.add_argument("--workload", default="L131071", choices=["L131071", "L16383", "L1048575", "LABS_L1023"],
+                    help="batch timed as the main line (default: the L=2^17-1 batch of the metric)")
     ap.add_argument("--plain-steps", type=int, default=4)
     ap.add_argument("--cpu-sample-s", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -65,7 +68,7 @@ def parse():
     ap.add_argument("--serving-compare", type=int, default=0,
                     help="serving study: also run this many requests at --serving-rate under each SM split "
                          "(fixed, by outstanding work, by live requests)")
-    ap.add_argument("--serving-policy", default="requests", choices=["requests", "work"],
+    ap.add_argument("--serving-policy", default="balanced", choices=["balanced", "requests", "work"],
                     help="SM split between the serving length classes")
     ap.add_argument("--ablation", action="store_true",
                     help="run only the control-parameter studies (alpha pairs; LS_lmt x FLIP_lmt) at reduced "
@@ -233,12 +236,15 @@ def stored_traffic(kernel: str, workload: str):
     return None
 
 
-def rank_specs(walks: int, rank: int):
-    """The walks one rank runs: the L=131071 workload with seeds offset by rank, so ranks never
-    share a walk (weak scaling: every rank keeps the same number of walks)."""
-    wl = W.batch_131071(walks=walks)
-    return wl, [W.WalkSpec(L=s.L, seed=s.seed + rank * walks, alpha1=s.alpha1, alpha2=s.alpha2, budget=s.budget)
-                for s in wl.walks]
+WORKLOADS = {"L131071": W.batch_131071, "L16383": W.batch_16383, "L1048575": W.batch_1048575,
+             "LABS_L1023": W.labs_1023}
+
+
+def rank_specs(walks: int, rank: int, workload: str = "L131071"):
+    """The walks one rank runs: the workload (by default L=131071) with seeds offset by rank, so
+    ranks never share a walk (weak scaling: every rank keeps the same number of walks)."""
+    wl = WORKLOADS[workload](walks=walks)
+    return wl, [dataclasses.replace(s, seed=s.seed + rank * walks) for s in wl.walks]
 
 
 def aggregate(local_ms: float, local_units: int, world: int, dist=None, device=None):
@@ -290,7 +296,7 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
 
-    wl, specs = rank_specs(args.walks, rank)
+    wl, specs = rank_specs(args.walks, rank, args.workload)
     L, N = specs[0].L, specs[0].N
     assert args.warmup + args.steps <= specs[0].budget and args.warmup >= 1
     need = sum(P.psl_walk_bytes(s.L, s.n_lmt, 0) for s in specs)
@@ -306,8 +312,8 @@ def run_ours(args):
     with P.Context(arena_tensor=arena, stream=stream, max_walks=len(specs), device=local) as ctx:
         # the first walks keep a per-step trace so that the FP32 score error can be stated
         n_traced = min(8, len(specs))
-        ids = [ctx.submit_ex(s.L, s.seed, s.alpha1, s.alpha2, s.budget, trace_cap=args.warmup + args.steps)
-               if q < n_traced else ctx.submit(s.L, s.seed, s.alpha1, s.alpha2, s.budget)
+        ids = [ctx.submit_ex(s.L, s.seed, s.alpha1, s.alpha2, s.budget, topk=s.topk,
+                             trace_cap=args.warmup + args.steps if q < n_traced else 0)
                for q, s in enumerate(specs)]
         ctx.step(1)             # admission and initialisation
         if args.hot_threads or args.hot_tile:
@@ -350,7 +356,7 @@ def run_ours(args):
     if not args.no_plain and rank == 0:
         with P.Context(form="plain", arena_bytes=P.psl_walk_bytes(L, N, 0) + (16 << 20), stream=stream,
                        max_walks=2, device=local) as pc:
-            pid = pc.submit(L, 0, 4, 13, 2000)
+            pid = pc.submit(L, 0, specs[0].alpha1, specs[0].alpha2, 2000)
             pc.step(1)
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
@@ -461,7 +467,8 @@ def run_ours(args):
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32 (exact i384 decisions)",
                 "data": "synthetic",
-                "config": {"workload": wl.name, "L": L, "walks_per_gpu": len(specs), "n_lmt": N, "alpha": "4/13",
+                "config": {"workload": wl.name, "L": L, "walks_per_gpu": len(specs), "n_lmt": N,
+                           "alpha": f"{specs[0].alpha1}/{specs[0].alpha2}",
                            "ls_lmt": W.LS_LMT, "flip_lmt": W.FLIP_LMT, "form": "batched",
                            "hot_kernel": {"threads": tuned[0], "tile_superblocks": tuned[1]} if tuned else "default",
                            "l2": "inputs larger than L2 (walk state %.1f GB per GPU)" % (need / 1e9)},
@@ -497,6 +504,10 @@ def run_ours(args):
     return 0
 
 
+SHARE_POLICIES = {"work": "proportional to outstanding work", "requests": "proportional to live requests",
+                  "balanced": "proportional to sqrt(work x requests)", None: "fixed 12/30/58%"}
+
+
 def run_serving_study(args):
     """Serving with continuous batching on one GPU: a finite trace of requests at the trace's
     arrival rate, far above capacity, so the queue saturates; the capacity in requests/s
@@ -525,8 +536,7 @@ def run_serving_study(args):
         half = len(lat) // 2
         return dict(res.summary(), rate_hz=rate, arrival_span_s=trace[-1].t_arrival, terms=terms,
                     terms_per_s=terms / res.wall_s, requests_per_s=n / res.wall_s,
-                    shares={"work": "proportional to outstanding work", "requests": "proportional to live requests",
-                            None: "fixed 12/30/58%"}[policy], clocks=clocks,
+                    shares=SHARE_POLICIES[policy], clocks=clocks,
                     p50_first_half_s=float(np.percentile(lat[:half], 50)) if half else None,
                     p50_second_half_s=float(np.percentile(lat[half:], 50)) if half else None,
                     p99_first_half_s=float(np.percentile(lat[:half], 99)) if half else None,
@@ -545,7 +555,7 @@ def run_serving_study(args):
     if args.serving_compare:
         # the same saturated requests under each SM split between the length classes
         line["share_policies_saturated"] = {str(p): leg(args.serving_compare, args.serving_rate, policy=p)
-                                            for p in (None, "work", "requests")}
+                                            for p in (None, "work", "requests", "balanced")}
     print(json.dumps(line), flush=True)
     return 0
 

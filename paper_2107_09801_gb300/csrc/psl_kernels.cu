@@ -496,10 +496,111 @@ __device__ __forceinline__ void select_one(WalkDev &W) {
   }
 }
 
+// The same selection by one warp, for windows of at most kSelectWarpN neighbours: the
+// compaction goes 32 positions at a time (ballot + popcount keeps scan order) and every
+// reduction is a shuffle, so many short walks are served at once without block barriers.
+constexpr int kSelectWarpN = 2048;
+
+__device__ __forceinline__ void select_warp(WalkDev &W) {
+  const int lane = threadIdx.x & 31;
+  if (W.status != kRunning) return;
+  const int N = (int)W.N;
+  float *score = W.score;
+  const uint32_t ksplit = W.ksplit;
+  if (ksplit > 1) {
+    // partial scores of the k-chunks, summed in chunk order
+    for (int i = lane; i < N; i += 32) {
+      float sc = W.score_part[i];
+      for (uint32_t c = 1; c < ksplit; c++) sc += W.score_part[(size_t)c * N + i];
+      score[i] = sc;
+    }
+    __syncwarp();
+  }
+  float m = FLT_MAX;
+  for (int i = lane; i < N; i += 32) m = fminf(m, score[i]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fminf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  const double B = score_bound(W.S_abs, W.alpha, W.L, ksplit);
+  const float thr = __double2float_ru((double)m + 2.0 * B);
+
+  // ordered compaction of {i : score <= thr}
+  uint32_t total = 0;
+  const uint32_t below = (1u << lane) - 1u;
+  for (int base = 0; base < N; base += 32) {
+    const int i = base + lane;
+    const bool in = i < N && score[i] <= thr;
+    const uint32_t bal = __ballot_sync(0xffffffffu, in);
+    if (in) W.cand[total + __popc(bal & below)] = (uint32_t)(i + 1);
+    total += __popc(bal);
+  }
+
+  // FP32 top-k beyond the certified set
+  const uint32_t topk = min(W.topk, 16u);
+  uint32_t extra[16];
+  uint32_t nextra = 0;
+  unsigned long long last = 0;
+  while (total + nextra < topk && total + nextra < (uint32_t)N) {
+    unsigned long long best = ~0ull;
+    for (int i = lane; i < N; i += 32) {
+      const float f = score[i];
+      if (f <= thr) continue;
+      const unsigned long long key = ((unsigned long long)float_order(f) << 32) | (uint32_t)i;
+      if (key > last) best = min(best, key);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(0xffffffffu, best, o));
+    last = best;
+    if (last == ~0ull) break;
+    extra[nextra++] = (uint32_t)(last & 0xffffffffu) + 1u;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    // merge the extra positions into the ascending candidate list
+    uint32_t n = total;
+    for (uint32_t e = 0; e < nextra; e++) {
+      const uint32_t v = extra[e];
+      uint32_t p = n;
+      while (p > 0 && W.cand[p - 1] > v) {
+        W.cand[p] = W.cand[p - 1];
+        p--;
+      }
+      W.cand[p] = v;
+      n++;
+    }
+    W.ncand = n;
+    W.score_min = m;
+    W.bound = (float)B;
+  }
+
+  // first minimum of psl_j in scan order
+  unsigned long long pk = ~0ull;
+  if (W.ktau_on) {
+    for (int i = lane; i < N; i += 32) {
+      const int p = W.pslj[i];
+      pk = min(pk, ((unsigned long long)(uint32_t)p << 32) | (uint32_t)(i + 1));
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) pk = min(pk, __shfl_xor_sync(0xffffffffu, pk, o));
+  if (lane == 0) {
+    W.win_psl = (pk == ~0ull) ? INT_MAX : (int)(pk >> 32);
+    W.win_psl_i = (uint32_t)(pk & 0xffffffffu);
+  }
+}
+
+// Windows above kSelectWarpN neighbours take a block each; the rest a warp each.
 __global__ void __launch_bounds__(1024) k_select(WalkDev *hdr, const uint32_t *active, const Schedule *sched) {
-  for (uint32_t a = blockIdx.x; a < sched->nactive; a += gridDim.x) {
+  const uint32_t nact = sched->nactive;
+  for (uint32_t a = blockIdx.x; a < nact; a += gridDim.x) {
+    WalkDev &W = hdr[active[a]];
+    if ((int)W.N <= kSelectWarpN) continue;  // the same reading in every thread of the block
     __syncthreads();
-    select_one(hdr[active[a]]);
+    select_one(W);
+  }
+  const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t a = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); a < nact; a += nwarps) {
+    WalkDev &W = hdr[active[a]];
+    if ((int)W.N <= kSelectWarpN) select_warp(W);
   }
 }
 

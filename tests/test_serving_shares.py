@@ -23,7 +23,7 @@ def test_shares_follow_outstanding_work():
 
 
 def test_idle_context_holds_no_share_and_the_rest_take_the_gpu():
-    sh = SmShares(152, 3, floor=8, hysteresis=0.0)
+    sh = SmShares(152, 3, floor=8, hysteresis=0.0, policy="work")
     settle(sh, [5, 5, 5])
     got = settle(sh, [5, 0, 0])
     assert got == [152, 0, 0]
@@ -43,7 +43,7 @@ def test_hysteresis_keeps_small_changes_out():
 
 
 def test_concurrent_updates_keep_the_split_within_the_device():
-    sh = SmShares(152, 3, floor=8, hysteresis=0.0)
+    sh = SmShares(152, 3, floor=8, hysteresis=0.0, policy="work")
 
     def run(i):
         for t in range(2000):
@@ -74,3 +74,12 @@ def test_unknown_policy_is_rejected():
     import pytest
     with pytest.raises(ValueError):
         SmShares(152, 3, policy="fair")
+
+
+def test_balanced_policy_sits_between_work_and_requests():
+    works, counts = [10**6, 10**9, 10**12], [30, 10, 20]
+    got = {p: settle(SmShares(152, 3, floor=8, hysteresis=0.0, policy=p), works, counts)
+           for p in ("work", "requests", "balanced")}
+    for c in range(3):
+        lo, hi = sorted((got["work"][c], got["requests"][c]))
+        assert lo <= got["balanced"][c] <= hi
