@@ -231,6 +231,10 @@ def _check_full_size(P, wl, steps, n_check, full_window=False, sample=48):
                 assert v > kv or (v == kv and pos[j] >= pos[int(last["kstar"])]), (q, j)
             if full_window and last["win_psl"] != 2**31 - 1:
                 assert last["win_psl"] == psls.min()
+            # best-PSL sequence: its PSL recomputed from scratch is psl_best
+            psl_b, sol = ctx.best(wid)
+            assert psl_b == st["psl_best"] == tr[-1]["psl_best"]
+            assert int(np.abs(fft_autocorr(sol)[1:]).max()) == psl_b
 
 
 def test_full_size_L16383_x4096(P):
@@ -243,6 +247,20 @@ def test_full_size_L131071_x1024(P):
 
 def test_full_size_L1048575_x148(P):
     _check_full_size(P, W.batch_1048575(), steps=1 + 1, n_check=1, sample=24)
+
+
+# whole budgets of the workloads on a few walks (phase switches included): the final pivot's
+# C, PSL and exact F, the best sequence, and the last decision against the oracle
+def test_full_budget_L16383_x8(P):
+    _check_full_size(P, W.batch_16383(walks=8), steps=10_000, n_check=3)
+
+
+def test_full_budget_L131071_x2(P):
+    _check_full_size(P, W.batch_131071(walks=2), steps=2000, n_check=2)
+
+
+def test_full_budget_L1048575_x1(P):
+    _check_full_size(P, W.batch_1048575(walks=1), steps=200, n_check=1, sample=24)
 
 
 # ------------------------------------------------------------------------------------------------
