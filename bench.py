@@ -406,7 +406,7 @@ def run_ours(args):
                 small[label] = time.perf_counter() - t0
                 small[label.replace("_s", "_psl_best")] = c1.poll(wid)["psl_best"]
 
-    # the other batch configurations of the survey: throughput only (a few timed steps each)
+    # the other batch configurations: throughput only (a few timed steps each)
     others = None
     if args.other_configs and rank == 0:
         others = {}
