@@ -584,12 +584,14 @@ def run_ablation(args):
                                "mean_psl": {f"{r.setting.alpha1}/{r.setting.alpha2}": r.mean for r in res},
                                "std_psl": {f"{r.setting.alpha1}/{r.setting.alpha2}": r.std for r in res},
                                "psl": {f"{r.setting.alpha1}/{r.setting.alpha2}": r.psl_best for r in res}}
-        t = time.perf_counter()
-        res = ls_flip_grid(ctx, L, args.grid_runs, int(args.grid_nse))
-        line["ls_flip_grid"] = {"runs": args.grid_runs, "nse_per_run": args.grid_nse,
-                                "moves_per_run": moves_for_nse(args.grid_nse, L), "alpha": "4/13",
-                                "wall_s": time.perf_counter() - t,
-                                "mean_psl": {f"LS{r.setting.ls_lmt}/FLIP{r.setting.flip_lmt}": r.mean for r in res}}
+        if args.grid_runs > 0:
+            t = time.perf_counter()
+            res = ls_flip_grid(ctx, L, args.grid_runs, int(args.grid_nse))
+            line["ls_flip_grid"] = {"runs": args.grid_runs, "nse_per_run": args.grid_nse,
+                                    "moves_per_run": moves_for_nse(args.grid_nse, L), "alpha": "4/13",
+                                    "wall_s": time.perf_counter() - t,
+                                    "mean_psl": {f"LS{r.setting.ls_lmt}/FLIP{r.setting.flip_lmt}": r.mean
+                                                 for r in res}}
     line["paper_context"] = {"scale": "L=65535, 30 runs, 10^10 NSE per run (A100)",
                              "alpha_table_mean_psl": {"4/13": 212.700, "4/4": 232.833, "13/13": 238.967}}
     print(json.dumps(line), flush=True)
