@@ -26,13 +26,14 @@ namespace psl {
 // the build (one thread per group, consecutive lanes on consecutive super-blocks) is free
 // of bank conflicts, and a lookup address is ((W >> s) & 0x7C) ^ (base_sb | swizzle) plus a
 // constant: one shift and one three-input logic op.  Regions are decided per warp and per
-// super-block, so the common case runs without per-group tests.
+// super-block, so the common case runs without per-group tests.  Block sums of at most 48
+// values are flushed into a compensated (hi, lo) pair.
 // ------------------------------------------------------------------------------------
 constexpr int kSbFloats = 576;           // 6 groups x 3 tables x 32 entries
 constexpr int kSbBytes = kSbFloats * 4;  // 2304 bytes = 18 x 128
 
 // tables (rounded up to a 128-byte boundary inside the allocation), two TMA staging
-// buffers of the tile's per-k values, and two ints
+// buffers of the tile's per-k values, and a few ints of block-wide state
 size_t hot_batched_smem(uint32_t tile_sb) { return (size_t)tile_sb * kSbBytes + 2 * (size_t)tile_sb * kSbK * 16 + 256; }
 
 // ---- TMA bulk copies and mbarriers (sm_90 and later) ----
@@ -432,16 +433,20 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem *items, Sche
     {
       int pu = j + kt0, pv = j - kt0 - 31;
       uint32_t bsw = bsw0;
-      for (; sb + 1 < n_int; sb += 2) {
-        sb_interior(a0, a1, bits, pu, pv, M, bsw);
-        sb_interior(a0, a1, bits, pu + kSbK, pv - kSbK, M, bsw + (kSbBytes + 4));
+      // eight super-blocks per flush: at most 48 additions into either accumulator
+      for (; sb + 7 < n_int; sb += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; u++)
+          sb_interior(a0, a1, bits, pu + u * kSbK, pv - u * kSbK, M, bsw + u * (kSbBytes + 4));
         flush2(hi, lo, a0, a1);
-        pu += 2 * kSbK, pv -= 2 * kSbK, bsw += 2 * (kSbBytes + 4);
+        pu += 8 * kSbK, pv -= 8 * kSbK, bsw += 8 * (kSbBytes + 4);
       }
       if (sb < n_int) {
-        sb_interior(a0, a1, bits, pu, pv, M, bsw);
+        for (; sb < n_int; sb++) {
+          sb_interior(a0, a1, bits, pu, pv, M, bsw);
+          pu += kSbK, pv -= kSbK, bsw += kSbBytes + 4;
+        }
         flush2(hi, lo, a0, a1);
-        sb++;
       }
     }
     const float4 *Ts = stage + (cq & 1u) * kTileK;  // this tile's per-k values, still staged
@@ -454,16 +459,19 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem *items, Sche
       const int step = plus_side ? kSbK : -kSbK;
       int pe = plus_side ? j + kt0 + sb * kSbK : j - kt0 - sb * kSbK - 31;
       uint32_t bsw = bsw0 + sb * (kSbBytes + 4);
-      for (; sb + 1 < n_edge; sb += 2) {
-        sb_edge(a0, a1, bits, pe, plus_side, M, bsw);
-        sb_edge(a0, a1, bits, pe + step, plus_side, M, bsw + (kSbBytes + 4));
+      // eight super-blocks per flush: at most 24 additions into either accumulator
+      for (; sb + 7 < n_edge; sb += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; u++) sb_edge(a0, a1, bits, pe + u * step, plus_side, M, bsw + u * (kSbBytes + 4));
         flush2(hi, lo, a0, a1);
-        pe += 2 * step, bsw += 2 * (kSbBytes + 4);
+        pe += 8 * step, bsw += 8 * (kSbBytes + 4);
       }
       if (sb < n_edge) {
-        sb_edge(a0, a1, bits, pe, plus_side, M, bsw);
+        for (; sb < n_edge; sb++) {
+          sb_edge(a0, a1, bits, pe, plus_side, M, bsw);
+          pe += step, bsw += kSbBytes + 4;
+        }
         flush2(hi, lo, a0, a1);
-        sb++;
       }
     }
     for (; sb < n_all; sb++) {
