@@ -477,7 +477,10 @@ def run_ours(args):
                              "traffic": stored_traffic("k_hot_batched", wl.name),
                              "peak_basis": f"{SM_COUNT_GB300} SMs x {LANES_PER_SM} lanes x {mhz:.0f} MHz "
                                            "(median SM clock sampled in the timed region)",
-                             "ops_basis": "2 lane-ops per (neighbour, shift) term, (L-1) terms per flip-eval"},
+                             "ops_basis": "2 lane-ops per (neighbour, shift) term, (L-1) terms per flip-eval",
+                             "note": "one shared-memory lookup scores 5 terms and terms without a partner are "
+                                     "skipped, so the kernel can run below 2 lane-ops per term and frac can pass "
+                                     "1; the hardware-side measure (issue slots, ALU/LSU pipes) is in profiles/"},
                 "clocks": clocks, "gpu_launches": launches, "kernels": kernels,
                 "fp32_score_error": fp32_err,
                 "plain": plain,
