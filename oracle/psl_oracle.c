@@ -314,7 +314,7 @@ static int param_check(const orc_params *p) {
     return 0;
 }
 
-/* Alg. 1 lines before the while loop. */
+/* Alg. 1: the initialisation before the search loop. */
 ORC_API int orc_init(const orc_params *p, orc_state *st) {
     if (param_check(p)) return -1;
     uint32_t L = p->L;

@@ -6,7 +6,7 @@ It contains none of the method's arithmetic: the search's own random draws are
 made by each implementation from its walk seed.
 
 The paper's workloads are uniform random +-1 starts at L = 2^m - 1
-(Sec. 4, Alg. 1 line "pivot <- Rand(L, SEED)") with N_lmt = 6912,
+(Sec. 4; the random start of Alg. 1) with N_lmt = 6912,
 LS_lmt = 2000, FLIP_lmt = 10, alpha1 = 4 and alpha2 = 13 (m <= 17) or
 10 (m = 20) (Sec. 4.1 and Table 3).  There is no dataset: these synthetic
 starts are the workload itself.
