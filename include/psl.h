@@ -8,7 +8,7 @@
  *   C_k = sum_{i=0}^{L-1-k} s_i s_{i+k}, k = 0..L-1                   (Eq. 2)
  *   PSL = max_{k=1..L-1} |C_k|                                        (Eq. 3, range read as 1..L-1)
  *   F_alpha = sum_{k=1}^{L-1} |C_k|^alpha                             (Eq. 4)
- * and runs Algorithm 1 ("Search algorithm"): every step scores a window of
+ * and runs the search of Algorithm 1: every step scores a window of
  * N = min(N_lmt, L) single-flip neighbours j = (start + i) % L, i = 1..N, with
  * start = Rand() % L, through the one-element flip update of Sec. 3
  * (C'_k = C_k - 2 s_j (s_{j+k} + s_{j-k}), absent partners counting 0), moves to
