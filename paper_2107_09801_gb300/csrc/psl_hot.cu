@@ -284,8 +284,9 @@ struct HotPipe {
 // Scores one work item (a block of window positions, possibly one k-chunk of them).  At the
 // start of its last tile thread 0 takes the next item from the schedule and, when that
 // item's walk is running, issues the copy of its first tile, so the copy overlaps this
-// tile.  Returns false when a staged copy timed out: the block must then stop taking work.
-template <int NT, int NSB>
+// tile.  FB super-blocks go into one block sum before each compensated flush.  Returns
+// false when a staged copy timed out: the block must then stop taking work.
+template <int NT, int NSB, int FB>
 __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem *items, Schedule *sched, const uint32_t item,
                                         HotPipe &pipe, uint32_t mbar_s, uint32_t *s_next) {
   static_assert(NSB <= 32, "the per-super-block swizzle assumes at most 32 super-blocks per tile");
@@ -433,13 +434,13 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem *items, Sche
     {
       int pu = j + kt0, pv = j - kt0 - 31;
       uint32_t bsw = bsw0;
-      // eight super-blocks per flush: at most 48 additions into either accumulator
-      for (; sb + 7 < n_int; sb += 8) {
+      // FB super-blocks per flush: at most 6 FB additions into either accumulator
+      for (; sb + FB - 1 < n_int; sb += FB) {
 #pragma unroll
-        for (int u = 0; u < 8; u++)
+        for (int u = 0; u < FB; u++)
           sb_interior(a0, a1, bits, pu + u * kSbK, pv - u * kSbK, M, bsw + u * (kSbBytes + 4));
         flush2(hi, lo, a0, a1);
-        pu += 8 * kSbK, pv -= 8 * kSbK, bsw += 8 * (kSbBytes + 4);
+        pu += FB * kSbK, pv -= FB * kSbK, bsw += FB * (kSbBytes + 4);
       }
       if (sb < n_int) {
         for (; sb < n_int; sb++) {
@@ -459,12 +460,12 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem *items, Sche
       const int step = plus_side ? kSbK : -kSbK;
       int pe = plus_side ? j + kt0 + sb * kSbK : j - kt0 - sb * kSbK - 31;
       uint32_t bsw = bsw0 + sb * (kSbBytes + 4);
-      // eight super-blocks per flush: at most 24 additions into either accumulator
-      for (; sb + 7 < n_edge; sb += 8) {
+      // FB super-blocks per flush: at most 3 FB additions into either accumulator
+      for (; sb + FB - 1 < n_edge; sb += FB) {
 #pragma unroll
-        for (int u = 0; u < 8; u++) sb_edge(a0, a1, bits, pe + u * step, plus_side, M, bsw + u * (kSbBytes + 4));
+        for (int u = 0; u < FB; u++) sb_edge(a0, a1, bits, pe + u * step, plus_side, M, bsw + u * (kSbBytes + 4));
         flush2(hi, lo, a0, a1);
-        pe += 8 * step, bsw += 8 * (kSbBytes + 4);
+        pe += FB * step, bsw += FB * (kSbBytes + 4);
       }
       if (sb < n_edge) {
         for (; sb < n_edge; sb++) {
@@ -524,7 +525,7 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem *items, Sche
 
 // Persistent: every block takes work items one by one from the schedule's counter
 // (longest walks first in the item list).
-template <int NT, int NSB>
+template <int NT, int NSB, int FB>
 __global__ void __launch_bounds__(NT, 1024 / NT) k_hot_batched(WalkDev *hdr, const HotItem *items, Schedule *sched) {
   __shared__ __align__(8) uint64_t s_mbar[2];
   __shared__ uint32_t s_next;
@@ -541,7 +542,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_hot_batched(WalkDev *hdr, con
     const uint32_t item = s_next;
     if (item >= sched->nitems) break;
     __syncthreads();  // every thread has read the item before it is replaced
-    if (!hot_one<NT, NSB>(hdr, items, sched, item, pipe, mbar_s, &s_next)) break;
+    if (!hot_one<NT, NSB, FB>(hdr, items, sched, item, pipe, mbar_s, &s_next)) break;
   }
 }
 
@@ -587,40 +588,49 @@ __global__ void __launch_bounds__(128) k_hot_plain(WalkDev *hdrp) {
   W.pslj[i - 1] = pj;
 }
 
-static uint32_t g_hot_blocks_per_sm[3][2];  // occupancy of every variant, measured at set-up
+static uint32_t g_hot_blocks_per_sm[3][2][2];  // occupancy of every variant, measured at set-up
 
 using HotFn = void (*)(WalkDev *, const HotItem *, Schedule *);
 
 static int variant_index(uint32_t threads) { return threads == 512 ? 2 : (threads == 128 ? 0 : 1); }
 
-static HotFn hot_variant(uint32_t threads, uint32_t tile_sb) {
-  if (threads == 512) return tile_sb == 16 ? k_hot_batched<512, 16> : k_hot_batched<512, 32>;
-  if (threads == 128) return tile_sb == 16 ? k_hot_batched<128, 16> : k_hot_batched<128, 32>;
-  return tile_sb == 16 ? k_hot_batched<256, 16> : k_hot_batched<256, 32>;
+template <int FB>
+static HotFn hot_variant_fb(uint32_t threads, uint32_t tile_sb) {
+  if (threads == 512) return tile_sb == 16 ? k_hot_batched<512, 16, FB> : k_hot_batched<512, 32, FB>;
+  if (threads == 128) return tile_sb == 16 ? k_hot_batched<128, 16, FB> : k_hot_batched<128, 32, FB>;
+  return tile_sb == 16 ? k_hot_batched<256, 16, FB> : k_hot_batched<256, 32, FB>;
+}
+
+static HotFn hot_variant(uint32_t threads, uint32_t tile_sb, uint32_t flush_sb) {
+  return flush_sb == 4 ? hot_variant_fb<4>(threads, tile_sb) : hot_variant_fb<8>(threads, tile_sb);
 }
 
 bool hot_config_supported(uint32_t threads, uint32_t tile_sb) {
   return (threads == 128 || threads == 256 || threads == 512) && (tile_sb == 16 || tile_sb == 32);
 }
 
+uint32_t hot_flush_for(uint32_t maxL) { return maxL >= 4096u ? 8u : 4u; }
+
 cudaError_t prepare_hot_kernels() {
   for (uint32_t t : {128u, 256u, 512u})
-    for (uint32_t sb : {16u, 32u}) {
-      HotFn f = hot_variant(t, sb);
-      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hot_batched_smem(sb));
-      if (e != cudaSuccess) return e;
-      int nb = 0;
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, (int)t, hot_batched_smem(sb));
-      if (e != cudaSuccess) return e;
-      g_hot_blocks_per_sm[variant_index(t)][sb == 32 ? 1 : 0] = (uint32_t)(nb > 0 ? nb : 1);
-    }
+    for (uint32_t sb : {16u, 32u})
+      for (uint32_t fb : {4u, 8u}) {
+        HotFn f = hot_variant(t, sb, fb);
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hot_batched_smem(sb));
+        if (e != cudaSuccess) return e;
+        int nb = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, (int)t, hot_batched_smem(sb));
+        if (e != cudaSuccess) return e;
+        g_hot_blocks_per_sm[variant_index(t)][sb == 32 ? 1 : 0][fb == 8 ? 1 : 0] = (uint32_t)(nb > 0 ? nb : 1);
+      }
   return cudaSuccess;
 }
 
 cudaError_t launch_hot_batched(const LaunchCtx &c) {
-  const uint32_t per_sm = g_hot_blocks_per_sm[variant_index(c.hot_threads)][c.hot_tile_sb == 32 ? 1 : 0];
-  hot_variant(c.hot_threads, c.hot_tile_sb)<<<per_sm * c.sm_count, c.hot_threads, hot_batched_smem(c.hot_tile_sb),
-                                              c.stream>>>(c.hdr, c.items, c.sched);
+  const uint32_t fb = c.hot_flush_sb == 4 ? 4u : 8u;
+  const uint32_t per_sm = g_hot_blocks_per_sm[variant_index(c.hot_threads)][c.hot_tile_sb == 32 ? 1 : 0][fb == 8 ? 1 : 0];
+  hot_variant(c.hot_threads, c.hot_tile_sb, fb)<<<per_sm * c.sm_count, c.hot_threads,
+                                                  hot_batched_smem(c.hot_tile_sb), c.stream>>>(c.hdr, c.items, c.sched);
   return cudaGetLastError();
 }
 

@@ -115,6 +115,7 @@ struct LaunchCtx {
   const HotItem *items;    // device list of neighbourhood blocks
   uint32_t hot_threads;    // neighbours per block of the batched kernel
   uint32_t hot_tile_sb;    // super-blocks per k-tile
+  uint32_t hot_flush_sb;   // super-blocks per block sum of the batched kernel (4 or 8)
   uint32_t sm_count;
   uint32_t maxL;           // longest walk of an initialisation launch
   uint32_t ninit;          // walks of an initialisation launch
@@ -135,6 +136,7 @@ cudaError_t launch_decide(const LaunchCtx &c);
 cudaError_t launch_start_init(const LaunchCtx &c);
 size_t hot_batched_smem(uint32_t tile_sb);
 bool hot_config_supported(uint32_t threads, uint32_t tile_sb);  // block sizes 128/256/512, tiles 16/32
+uint32_t hot_flush_for(uint32_t maxL);  // super-blocks per block sum for a batch whose longest walk is maxL
 
 // Candidate threshold shared bit-for-bit by the device select and the host select
 // of the plain form.  Returns the largest FP32 score that may still belong to the

@@ -144,6 +144,7 @@ struct psl_ctx {
   bool active_dirty = true;
   uint32_t nitems = 0, max_chunk_apply = 1, max_chunk_rc = 1;
   int64_t next_id = 0;
+  uint32_t hot_flush_sb = 8;  // super-blocks per block sum of the neighbourhood kernel
   uint32_t sm_count = 152;   // SMs the persistent kernels are sized for
   uint32_t dev_sms = 152;    // SMs of the device
   std::string err;
@@ -470,6 +471,17 @@ static int rebuild_active(psl_ctx *ctx) {
   std::vector<HotItem> items;
   ctx->max_chunk_apply = 1;
   ctx->max_chunk_rc = 1;
+  // short walks run their few super-blocks with shorter block sums (less unrolled code)
+  uint32_t maxL = 0;
+  for (uint32_t s : ctx->active) maxL = std::max(maxL, ctx->h_hdr[s].L);
+  const uint32_t fb = hot_flush_for(maxL);
+  if (fb != ctx->hot_flush_sb) {
+    ctx->hot_flush_sb = fb;
+    if (ctx->graph) {  // captured with the other kernel variant
+      cudaGraphExecDestroy(ctx->graph);
+      ctx->graph = nullptr;
+    }
+  }
   // Split every walk's k range into chunks when the neighbour blocks alone would leave
   // SMs idle (few walks, or a long walk on its own): aim for about four blocks per SM.
   const uint32_t T_ = (uint32_t)ctx->cfg.hot_threads;
@@ -532,6 +544,7 @@ static LaunchCtx launch_ctx(psl_ctx *ctx, const uint32_t *d_list, Schedule *d_sc
   c.items = ctx->d_items;
   c.hot_threads = (uint32_t)ctx->cfg.hot_threads;
   c.hot_tile_sb = (uint32_t)ctx->cfg.hot_tile_sb;
+  c.hot_flush_sb = ctx->hot_flush_sb;
   c.sm_count = ctx->sm_count;
   c.stream = ctx->stream;
   return c;
