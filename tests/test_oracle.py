@@ -200,6 +200,50 @@ def test_flip_update_equals_recompute_large():
 
 
 # --------------------------------------------------------------------------------------------
+# Alg. 1 neighbourhood evaluation without a move (the checker of the full-size GPU checks):
+# every neighbour's exact F (Eq. 4) and PSL (Eq. 3) against the flipped sequence rebuilt
+# from scratch by the FFT route and scored with Python integers
+# --------------------------------------------------------------------------------------------
+def _neighbour_psl_plus4(s, C):
+    """Positions j whose neighbour has a sidelobe of magnitude PSL + 4 (the largest a single
+    flip can reach), found by the flip rule of Sec. 3 written out in numpy."""
+    L, P = len(s), int(np.abs(C[1:]).max())
+    out = []
+    for j in range(L):
+        k = np.arange(1, L)
+        part = np.where(j + k < L, s[np.minimum(j + k, L - 1)], 0) + np.where(j - k >= 0, s[np.maximum(j - k, 0)], 0)
+        if int(np.abs(C[1:] - 2 * int(s[j]) * part).max()) == P + 4:
+            out.append(j)
+    return out
+
+
+@pytest.mark.parametrize("L,alpha,sample", [(13, 4, None), (13, 16, None), (300, 1, None), (300, 16, None),
+                                            (300, 13, None), (4096, 4, 48), (4096, 16, 24)])
+def test_eval_neighbours_against_recompute(L, alpha, sample):
+    s = W.random_pm1(L, 7 * L + alpha)
+    C = O.autocorr(s)
+    js = list(range(L))
+    if sample:
+        rng = np.random.Generator(np.random.PCG64(L + alpha))
+        js = sorted(set(rng.choice(L, size=sample, replace=False).tolist()) | {0, 1, L // 2, L - 2, L - 1})
+    plus4 = _neighbour_psl_plus4(s, C) if L <= 300 else []
+    if L == 300:
+        assert plus4, "no neighbour reaches PSL + 4: the +4 headroom of the power table is not exercised"
+        js = sorted(set(js) | set(plus4))
+    vals, psls = O.eval_neighbours(s, C, alpha, js)
+    for j, v, p in zip(js, vals, psls):
+        t = s.copy()
+        t[j] = -t[j]
+        Cn = fft_autocorr(t)
+        assert v == py_fitness(Cn, alpha), (L, alpha, j)
+        assert p == int(np.abs(Cn[1:]).max()), (L, alpha, j)
+    # the neighbours' order is kept and the pivot itself is untouched
+    vals_rev, _ = O.eval_neighbours(s, C, alpha, js[::-1])
+    assert vals_rev == vals[::-1]
+    assert np.array_equal(O.autocorr(s), C)
+
+
+# --------------------------------------------------------------------------------------------
 # Algorithm 1: one decision against brute force over the window
 # --------------------------------------------------------------------------------------------
 @pytest.mark.parametrize("L,n_lmt,alpha", [(13, 13, 4), (31, 10, 13), (63, 63, 1), (63, 5, 2), (100, 40, 16)])

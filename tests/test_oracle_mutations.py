@@ -32,6 +32,13 @@ MUTATIONS = [
     ("fbest_ignores_moves", "memcpy(st->F, value_step.w, sizeof st->F);\n        note_pivot(p, st);",
      "memcpy(st->F, value_step.w, sizeof st->F);"),
     ("fbest_kept_with_two_alphas", "if (p->alpha1 != p->alpha2) return;", "if (p->alpha1 == 0) return;"),
+    ("eval_nb_power_table_no_headroom", "power_table(max_abs_sidelobe(C, L) + 4, alpha)",
+     "power_table(max_abs_sidelobe(C, L), alpha)"),
+    ("eval_nb_neighbour_index_offset", "orc_flip_autocorr(s, C, L, js[q], Cn);",
+     "orc_flip_autocorr(s, C, L, (js[q] + 1) % L, Cn);"),
+    ("eval_nb_psl_of_pivot", "if (psl_out) psl_out[q] = orc_psl(Cn, L);", "if (psl_out) psl_out[q] = orc_psl(C, L);"),
+    ("eval_nb_limb_offset", "memcpy(limbs_out + (size_t)q * WL, v.w, sizeof v.w);",
+     "memcpy(limbs_out + (size_t)q * WL + 1, v.w, sizeof v.w - 8);"),
     ("transposed_pair", "c += (int32_t)s[i] * (int32_t)s[i + k];", "c += (int32_t)s[i] * (int32_t)s[L - 1 - i];"),
 ]
 
