@@ -38,8 +38,6 @@ import psl_workloads as W  # noqa: E402
 METRIC = "flip evals/s at L=2^17−1 (batched vs plain); p50/p99 serving latency"
 UNIT = "flip-evals/s"
 PAPER_A100_L131071 = 638043  # Table 4 of the paper: one walk on an A100 SXM4 (context only)
-SM_COUNT_GB300 = 152
-LANES_PER_SM = 128
 
 
 def parse():
@@ -58,8 +56,13 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--other-configs", type=int, default=1, help="also time the L=16383 x 4096 and L=1048575 x 148 batches")
-    ap.add_argument("--serving", type=int, default=24, help="requests of the serving trace to run (0: skip)")
+    ap.add_argument("--serving", type=int, default=100,
+                    help="requests of the serving trace run at 0.8x the capacity measured by the probe (0: skip)")
+    ap.add_argument("--serving-probe", type=int, default=40,
+                    help="requests of the saturated probe (arrivals at --serving-rate) that measures the capacity")
     ap.add_argument("--serving-rate", type=float, default=200.0)
+    ap.add_argument("--graph-steps", type=int, default=0,
+                    help="steps per CUDA graph launch in the timed region (0: all timed steps, at most 50)")
     ap.add_argument("--serving-study", type=int, default=0,
                     help="run only the serving study on this many requests: the trace at --serving-rate "
                          "(saturated), then at 0.8x the measured capacity; prints its own JSON line")
@@ -223,14 +226,15 @@ def kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def stored_traffic(kernel: str, workload: str):
-    """DRAM bytes per launch from an ncu capture, only if taken on the current kernel source."""
+def stored_counters(kernel: str, workload: str):
+    """Per-launch ncu counters of a kernel (DRAM bytes, warp instructions), only if they were
+    taken on the current kernel source."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         d = json.load(open(p))
         rec = d[kernel][workload]
         if rec.get("source_hash") == kernel_source_hash():
-            return rec["bytes_per_launch"]
+            return rec
     except Exception:
         pass
     return None
@@ -281,6 +285,93 @@ def fp32_error_stats(traces) -> dict:
     return {"moves_checked": n, "max_err_over_bound": worst, "max_rel_err": worst_rel}
 
 
+def term_counts(L: int) -> dict:
+    """Per flip-eval, averaged over the neighbour position j (a window start is uniform):
+    nominal terms L-1; live terms (shifts with at least one partner: k <= max(j, L-1-j));
+    and the lookups of the neighbourhood kernel's tables (two per 5 two-partner shifts, one
+    per 5 one-partner shifts)."""
+    j = np.arange(L, dtype=np.float64)
+    kin = np.minimum(j, L - 1 - j)
+    kout = np.maximum(j, L - 1 - j)
+    return {"nominal": float(L - 1), "live": float(kout.mean()),
+            "lookups": float((2.0 * kin / 5.0 + (kout - kin) / 5.0).mean())}
+
+
+def measure_alu_peak(local: int, stream) -> dict:
+    """The microbenchmarks of the CUDA-core pipes (psl_alu_peak) with the SM clock sampled
+    while they run."""
+    from paper_2107_09801_gb300 import binding as B
+    clk = ClockSampler(local)
+    clk.start()
+    pk = B.psl_alu_peak(local, stream.cuda_stream)
+    pk["clocks"] = clk.stop()
+    return pk
+
+
+def hot_roofline(walks_x_N: int, L: int, hot_avg_ms: float, peak: dict, mhz_run: float, counters) -> dict:
+    """Roofline of the neighbourhood kernel: 2 lane-ops per (neighbour, shift) term against the
+    measured FP32-add / integer-add / logic-op mix rate, scaled to the clock of the timed region;
+    also on live terms, and against the lookup ceiling of the kernel's own inner pattern."""
+    tc = term_counts(L)
+    mhz_peak = peak["clocks"].get("sm_mhz") or peak["max_clock_mhz"]
+    scale = (mhz_run / mhz_peak) if (mhz_run and mhz_peak) else 1.0
+    p_mix = peak["mix"] * scale
+    p_lookup = peak["lookup"] * scale
+    sec = hot_avg_ms / 1000.0
+    achieved = walks_x_N * 2 * tc["nominal"] / sec
+    achieved_live = walks_x_N * 2 * tc["live"] / sec
+    lookups = walks_x_N * tc["lookups"] / sec
+    out = {"bound": "alu", "kernel": "k_hot_batched", "achieved": achieved / 1e12, "peak": p_mix / 1e12,
+           "unit": "Tops/s", "frac": achieved / p_mix,
+           "peak_basis": f"measured: psl_alu_peak mix microbenchmark (FP32 add, integer add, logic op 1:1:1 on "
+                         f"{peak['sm_count']} SMs) {peak['mix'] / 1e12:.2f} Tops/s at {mhz_peak:.0f} MHz, scaled to "
+                         f"the timed region's {mhz_run:.0f} MHz",
+           "ops_basis": "2 lane-ops per (neighbour, shift) term, (L-1) terms per flip-eval",
+           "frac_live_terms": achieved_live / p_mix,
+           "live_basis": f"2 lane-ops per term with a partner: {tc['live']:.0f} of {tc['nominal']:.0f} shifts per "
+                         "flip-eval on average",
+           "lookup_ceiling": {"lookups_per_s_measured": peak["lookup"], "lookups_per_flip_eval": tc["lookups"],
+                              "flip_evals_per_s_ceiling": p_lookup / tc["lookups"],
+                              "frac": lookups / p_lookup},
+           "traffic": None, "issue_frac": None}
+    if counters:
+        out["traffic"] = counters.get("bytes_per_launch")
+        if counters.get("warp_inst_per_launch") and peak.get("sm_count"):
+            # 4 schedulers per SM, one warp instruction each per clock
+            issue_peak = peak["sm_count"] * 4 * mhz_run * 1e6
+            out["issue_frac"] = counters["warp_inst_per_launch"] / sec / issue_peak
+    return out
+
+
+def serving_leg(args, local, sms):
+    """Continuous batching at a sustainable rate: a saturated probe of the serving trace measures
+    the capacity (requests / wall time), then requests arrive at 0.8x that capacity."""
+    import paper_2107_09801_gb300 as P
+    from paper_2107_09801_gb300.serving import serve_classes
+
+    def leg(n, rate, offset=0):
+        trace = W.serving_trace(n_requests=n + offset, rate_hz=rate)[offset:]
+        t0 = trace[0].t_arrival
+        trace = [W.Request(r.t_arrival - t0, r.spec) for r in trace]
+        arena = min(24 << 30, int(sum(P.psl_walk_bytes(r.spec.L, r.spec.n_lmt, 0) for r in trace) * 1.5) + (256 << 20))
+        res = serve_classes(trace, arena, sm_count=sms, ctx_kwargs=dict(device=local),
+                            share_policy=args.serving_policy)
+        return res, trace
+
+    probe, _ = leg(args.serving_probe, args.serving_rate)
+    capacity = args.serving_probe / probe.wall_s
+    rate = 0.8 * capacity
+    res, trace = leg(args.serving, rate, offset=args.serving_probe)   # requests not seen by the probe
+    return dict(res.summary(), rate_hz=rate, capacity_requests_per_s=capacity,
+                capacity_basis=f"saturated probe: {args.serving_probe} requests arriving at {args.serving_rate} "
+                               f"req/s, completed in {probe.wall_s:.1f} s (p50 {probe.summary()['p50_s']:.2f} s)",
+                arrival_span_s=trace[-1].t_arrival,
+                trace="Poisson arrivals at 0.8x capacity, m~U{10..20}, budgets ~U{100..10^4}, alpha1~U{2..6}, "
+                      "alpha2~U{alpha1+4..13}, request r has seed r",
+                classes="L<=2^14, <=2^17, <=2^20: one context, stream and host thread each; SMs split by "
+                        f"{args.serving_policy} (8-SM floor per busy class)")
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -295,10 +386,13 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
 
     wl, specs = rank_specs(args.walks, rank, args.workload)
     L, N = specs[0].L, specs[0].N
-    assert args.warmup + args.steps <= specs[0].budget and args.warmup >= 1
+    G = args.graph_steps or min(args.steps, 50)
+    K2 = min(args.steps, 10)
+    assert args.warmup + args.steps + K2 + 2 <= specs[0].budget and args.warmup >= 1
     need = sum(P.psl_walk_bytes(s.L, s.n_lmt, 0) for s in specs)
     arena = torch.empty(int(need * 1.1) + (64 << 20), dtype=torch.uint8, device=dev)
 
@@ -308,12 +402,12 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    out = {}
+    peak = measure_alu_peak(local, stream)
     with P.Context(arena_tensor=arena, stream=stream, max_walks=len(specs), device=local) as ctx:
         # the first walks keep a per-step trace so that the FP32 score error can be stated
         n_traced = min(8, len(specs))
         ids = [ctx.submit_ex(s.L, s.seed, s.alpha1, s.alpha2, s.budget, topk=s.topk,
-                             trace_cap=args.warmup + args.steps if q < n_traced else 0)
+                             trace_cap=args.warmup + args.steps + K2 + 2 if q < n_traced else 0)
                for q, s in enumerate(specs)]
         ctx.step(1)             # admission and initialisation
         if args.hot_threads or args.hot_tile:
@@ -322,34 +416,50 @@ def run_ours(args):
         else:
             tuned = ctx.autotune(reps=2) if not args.no_autotune else None
         ctx.step(args.warmup - 1)
+        # the timed steps run from a CUDA graph of G steps, captured here (no step runs), with
+        # event-record nodes around the neighbourhood kernel only
+        ctx.profile(2)
+        ctx.set_steps_per_graph(G)
         barrier()
         clk = ClockSampler(local)
         clk.start()
-        ctx.profile(True)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         ctx.step(args.steps)
         e1.record(stream)
         barrier()
-        prof = ctx.profile_read()
-        ctx.profile(False)
         clocks = clk.stop()
+        prof = ctx.profile_read()
+        ctx.profile(0)
         ms = e0.elapsed_time(e1)
+        # the same steps as plain launches (no graph, no events), for comparison
+        ctx.set_steps_per_graph(0)
+        barrier()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        ctx.step(K2)
+        p1.record(stream)
+        barrier()
+        ms_plain_launch = p0.elapsed_time(p1)
+        # per-kernel breakdown, untimed: every kernel between its own events
+        ctx.profile(1)
+        ctx.step(2)
+        breakdown = ctx.profile_read()
+        ctx.profile(0)
         st = [ctx.poll(i) for i in ids[:4]]
-        assert all(s["moves"] == args.warmup + args.steps for s in st)
+        assert all(s["moves"] == args.warmup + args.steps + K2 + 2 for s in st)
         fp32_err = fp32_error_stats([ctx.trace(i, args.warmup + args.steps) for i in ids[:n_traced]])
     flip_evals_rank = len(specs) * N * args.steps
     value, ms_max = aggregate(ms, flip_evals_rank, world, dist, dev)
 
-    # roofline of the dominant kernel (the neighbourhood score), live durations
+    # roofline of the dominant kernel (the neighbourhood score), live durations in the timed region
     n_hot, hot_ms = prof.get("hot", (0, 0.0))
     hot_avg_ms = hot_ms / max(n_hot, 1)
-    ops_per_launch = len(specs) * N * 2 * (L - 1)        # 2 lane-ops per (j, k) term, (L-1) terms
-    achieved = ops_per_launch / (hot_avg_ms / 1000.0)
-    mhz = clocks.get("sm_mhz") or 2070.0
-    peak = SM_COUNT_GB300 * LANES_PER_SM * mhz * 1e6
-    kernels = {k: {"launches": n, "avg_ms": (ms_ / n if n else 0.0)} for k, (n, ms_) in prof.items() if n}
-    launches = sum(n for k, (n, _) in prof.items() if k != "init")
+    mhz = clocks.get("sm_mhz") or peak["max_clock_mhz"]
+    roof = hot_roofline(len(specs) * N, L, hot_avg_ms, peak, mhz, stored_counters("k_hot_batched", wl.name))
+    roof["hot_launches_timed"] = n_hot
+    kernels = {k: {"launches": n, "avg_ms": (ms_ / n if n else 0.0)} for k, (n, ms_) in breakdown.items() if n}
+    launches = args.steps * 5     # hot, select, recheck, decide, apply per step
 
     # plain form: one walk per launch, one thread per neighbour, host-side selection
     plain = None
@@ -366,30 +476,32 @@ def run_ours(args):
             plain = {"value": N * args.plain_steps / dt, "walks": 1, "steps": args.plain_steps,
                      "ms_per_step": 1000 * dt / args.plain_steps}
 
-    # end to end through the public API: submit from the host, run, read every walk's
-    # status and best sequence back into host memory
+    # end to end through the public API: submit from the host, initialise, run the steps from a
+    # CUDA graph, read every walk's status and best sequence back into host memory; the bytes
+    # are the library's own count of what it copied
     e2e = None
     if not args.no_e2e:
         barrier()
         t0 = time.perf_counter()
         hot = dict(hot_threads=tuned[0], hot_tile_sb=tuned[1]) if tuned else {}
-        with P.Context(arena_tensor=arena, stream=stream, max_walks=len(specs), device=local, **hot) as ctx:
+        with P.Context(arena_tensor=arena, stream=stream, max_walks=len(specs), device=local,
+                       steps_per_graph=G, **hot) as ctx:
             ids = [ctx.submit(s.L, s.seed, s.alpha1, s.alpha2, s.budget) for s in specs]
             ctx.step(args.steps)
             psl_sum = 0
             for i in ids:
                 p, seq = ctx.best(i)
                 psl_sum += p
+            h2d, d2h = ctx.transfer_bytes()
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
         td = torch.tensor([dt], device=dev)
         if world > 1:
             dist.all_reduce(td, op=dist.ReduceOp.MAX)
-        hdr_bytes = 512
         e2e = {"value": world * flip_evals_rank / float(td.item()), "unit": UNIT,
-               "h2d_bytes_per_step": (len(specs) * (hdr_bytes + 64)) / args.steps,
-               "d2h_bytes_per_step": (len(specs) * hdr_bytes * args.steps + len(specs) * L) / args.steps,
-               "includes": "submit, walk initialisation, steps, status and best-sequence readback"}
+               "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
+               "bytes_counted": "by the library at each host<->device copy (psl_transfer_bytes)",
+               "includes": "submit, walk initialisation, graph capture, steps, status and best-sequence readback"}
 
     # the small configuration: L = 1023, one walk from seed 1, N = L, 2000 moves, time to budget
     small = None
@@ -406,7 +518,7 @@ def run_ours(args):
                 small[label] = time.perf_counter() - t0
                 small[label.replace("_s", "_psl_best")] = c1.poll(wid)["psl_best"]
 
-    # the other batch configurations: throughput only (a few timed steps each)
+    # the other batch configurations: throughput only (a few timed steps each, from a graph)
     others = None
     if args.other_configs and rank == 0:
         others = {}
@@ -423,13 +535,16 @@ def run_ours(args):
                 t_init = time.perf_counter() - t_init
                 tune_o = oc.autotune(reps=1)
                 oc.step(2)
-                oc.profile(True)
+                oc.profile(2)
+                oc.set_steps_per_graph(k_o)
+                torch.cuda.synchronize(dev)
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
                 oc.step(k_o)
                 e1.record(stream)
                 torch.cuda.synchronize(dev)
                 prof_o = oc.profile_read()
+                oc.profile(0)
                 ms_o = e0.elapsed_time(e1)
                 quality = None
                 if specs_o[0].alpha1 == specs_o[0].alpha2 == 2:
@@ -440,27 +555,22 @@ def run_ours(args):
                                "merit_factor_best": float(np.max(mf))}
             Lo, No = specs_o[0].L, specs_o[0].N
             n_hot, hot_ms_o = prof_o.get("hot", (0, 0.0))
+            roof_o = hot_roofline(len(specs_o) * No, Lo, hot_ms_o / max(n_hot, 1), peak, mhz, None)
             others[wl_o.name] = {"value": len(specs_o) * No * k_o / (ms_o / 1000.0), "unit": UNIT,
-                                 "ms_per_step": ms_o / k_o, "steps": k_o,
-                                 "hot_kernel": {"threads": tune_o[0], "tile_superblocks": tune_o[1]},
-                                 "roofline_frac": (len(specs_o) * No * 2 * (Lo - 1)) / (hot_ms_o / max(n_hot, 1) / 1000.0) / peak,
+                                 "ms_per_step": ms_o / k_o, "steps": k_o, "graph_steps": k_o,
+                                 "hot_kernel": {"threads": tune_o[0], "tile_superblocks": tune_o[1],
+                                                "avg_ms": hot_ms_o / max(n_hot, 1)},
+                                 "roofline_frac": roof_o["frac"], "roofline_frac_live_terms": roof_o["frac_live_terms"],
+                                 "lookup_ceiling_frac": roof_o["lookup_ceiling"]["frac"],
                                  "init_s": t_init, "description": wl_o.description}
             if quality:
                 others[wl_o.name]["quality"] = quality
 
-    # serving: Poisson arrivals of walks with L = 2^m - 1, m uniform in 10..20, continuous batching
+    # serving: Poisson arrivals of walks with L = 2^m - 1, m uniform in 10..20, continuous batching,
+    # at 0.8x the capacity a saturated probe measures
     serving = None
     if args.serving > 0 and rank == 0:
-        from paper_2107_09801_gb300.serving import serve_classes
-        trace = W.serving_trace(n_requests=args.serving, rate_hz=args.serving_rate)
-        arena_s = min(24 << 30, int(sum(P.psl_walk_bytes(r.spec.L, r.spec.n_lmt, 0) for r in trace) * 1.5) + (256 << 20))
-        sms = torch.cuda.get_device_properties(dev).multi_processor_count
-        res = serve_classes(trace, arena_s, sm_count=sms, ctx_kwargs=dict(device=local),
-                            share_policy=args.serving_policy)
-        serving = dict(res.summary(), rate_hz=args.serving_rate, trace="Poisson arrivals, m~U{10..20}, budgets "
-                       "~U{100..10^4}, alpha1~U{2..6}, alpha2~U{alpha1+4..13}, request r has seed r",
-                       arena_gb=arena_s / 1e9, classes="L<=2^14, <=2^17, <=2^20: one context, stream and host "
-                       f"thread each; SMs split by {args.serving_policy} (8-SM floor per busy class)")
+        serving = serving_leg(args, local, sms)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -470,18 +580,16 @@ def run_ours(args):
                 "config": {"workload": wl.name, "L": L, "walks_per_gpu": len(specs), "n_lmt": N,
                            "alpha": f"{specs[0].alpha1}/{specs[0].alpha2}",
                            "ls_lmt": W.LS_LMT, "flip_lmt": W.FLIP_LMT, "form": "batched",
+                           "timed_path": f"CUDA graph of {G} steps per launch, event-record nodes around the "
+                                         "neighbourhood kernel only",
                            "hot_kernel": {"threads": tuned[0], "tile_superblocks": tuned[1]} if tuned else "default",
                            "l2": "inputs larger than L2 (walk state %.1f GB per GPU)" % (need / 1e9)},
-                "roofline": {"bound": "alu", "kernel": "k_hot_batched", "achieved": achieved / 1e12,
-                             "peak": peak / 1e12, "unit": "Tops/s", "frac": achieved / peak,
-                             "traffic": stored_traffic("k_hot_batched", wl.name),
-                             "peak_basis": f"{SM_COUNT_GB300} SMs x {LANES_PER_SM} lanes x {mhz:.0f} MHz "
-                                           "(median SM clock sampled in the timed region)",
-                             "ops_basis": "2 lane-ops per (neighbour, shift) term, (L-1) terms per flip-eval",
-                             "note": "one shared-memory lookup scores 5 terms and terms without a partner are "
-                                     "skipped, so the kernel can run below 2 lane-ops per term and frac can pass "
-                                     "1; the hardware-side measure (issue slots, ALU/LSU pipes) is in profiles/"},
+                "roofline": roof,
+                "alu_peak": {k: v for k, v in peak.items()},
                 "clocks": clocks, "gpu_launches": launches, "kernels": kernels,
+                "plain_launches": {"value": len(specs) * N * K2 / (ms_plain_launch / 1000.0), "steps": K2,
+                                   "ms_per_step": ms_plain_launch / K2,
+                                   "note": "the same batch and kernels launched one by one (no graph)"},
                 "fp32_score_error": fp32_err,
                 "plain": plain,
                 "batched_over_plain": (value / world) / plain["value"] if plain else None,

@@ -202,13 +202,52 @@ typedef struct {
   double total_ms;          /* sum of CUDA-event durations measured on the context's stream */
 } psl_kernel_time;
 
-/* Enables (1) or disables (0) CUDA-event timing of every kernel launch of psl_step
- * (launches captured in CUDA graphs are timed as one unit under "graph").
- * Enabling resets the totals. */
+/* Enables CUDA-event timing of the kernel launches of psl_step: 1 every kernel, 2 the
+ * neighbourhood-score kernel only (and whole graph launches), 0 off.  Steps run from a CUDA
+ * graph are timed by event-record nodes inside the graph (the graph is captured again when
+ * the mode changes), and the stream is synchronised after each graph launch to read them;
+ * every graph launch is also timed as one unit under "graph".  Enabling resets the totals;
+ * PSL_EINVAL for other values. */
 PSL_API int psl_profile(psl_ctx *ctx, int enable);
 
 /* Copies up to cap per-kernel totals; returns the number of kernel families. */
 PSL_API int psl_profile_read(psl_ctx *ctx, psl_kernel_time *out, size_t cap);
+
+/* Bytes the context has copied from host to device (*h2d) and from device to host (*d2h)
+ * since psl_init: walk headers, schedules, start sequences, status readback, best
+ * sequences, traces, exported state.  Either pointer may be NULL.  Counted at each copy,
+ * not estimated.  PSL_EINVAL for a null ctx. */
+PSL_API int psl_transfer_bytes(psl_ctx *ctx, uint64_t *h2d, uint64_t *d2h);
+
+/* Sets how many steps of the batched form one CUDA graph launch runs (0 = plain launches)
+ * and, when walks are running, captures that graph now, so that a later psl_step only
+ * launches it (the capture reads the device schedule, so it serves any later batch
+ * composition).  A graph captured while profiling is enabled carries event-record nodes
+ * around the kernels the profile mode times.  PSL_EINVAL for the plain form or steps < 0;
+ * PSL_ECUDA if the capture fails. */
+PSL_API int psl_set_steps_per_graph(psl_ctx *ctx, int32_t steps);
+
+/* Measured issue rates of the CUDA-core pipes that bound the neighbourhood kernel (no
+ * counterpart in the paper: the denominator of its roofline).  Four kernels fill every SM
+ * of the device for a few tens of milliseconds each, timed with CUDA events on stream.
+ * Rates are per second over the whole device, at whatever SM clock the device ran. */
+typedef struct {
+  int32_t sm_count;         /* cudaDevAttrMultiProcessorCount                              */
+  int32_t max_clock_mhz;    /* cudaDevAttrClockRate                                        */
+  int32_t blocks_per_sm;    /* resident blocks of the microbenchmark kernels                */
+  int32_t threads_per_block;
+  double fadd;              /* FP32 adds per second (independent chains)                    */
+  double alu;               /* integer adds and three-input logic ops per second, 1:1     */
+  double mix;               /* FP32 add, integer add and logic op 1:1:1, lane-ops per second */
+  double lookup;            /* the neighbourhood kernel's inner pattern (shift, logic op forming a
+                               table address, shared-memory load, FP32 add): lookups per second */
+  double ms[4];             /* duration of the timed launch of each (fadd, alu, mix, lookup) */
+} psl_alu_peak_t;
+
+/* Runs the microbenchmarks on device (stream: a cudaStream_t of that device, or NULL) and
+ * fills *out.  Makes device current.  PSL_EINVAL for a null out or device < 0; PSL_ECUDA
+ * if a launch fails. */
+PSL_API int psl_alu_peak(int32_t device, void *stream, psl_alu_peak_t *out);
 
 /* Autotuner of the batched form: admits queued walks, then times every supported
  * configuration of the neighbourhood kernel (neighbours per block 128/256/512 x k-tile
@@ -248,9 +287,12 @@ PSL_API int psl_set_max_sms(psl_ctx *ctx, int32_t max_sms);
  * Eq. 2 for one sequence already in device memory, computed with a scratch area built
  * into the library (128 KiB per device, held until the process exits) instead of
  * allocating.  seq_dev: device array of L int8 values (negative means -1, anything else
- * +1); C_dev: device array of L int32 receiving C_0..C_{L-1}; stream: a cudaStream_t or
- * NULL.  Requires 1 <= L <= 2^20 - 1 (PSL_EINVAL otherwise, and for NULL pointers);
- * PSL_ECUDA if the scratch lookup or a launch fails.  Calls no allocator.  Work is queued
+ * +1); C_dev: device array of L int32 receiving C_0..C_{L-1}; stream: a cudaStream_t of
+ * the current device (cudaGetDevice; the scratch used is that device's), or NULL.
+ * Requires 1 <= L <= 2^20 - 1 (PSL_EINVAL otherwise, and for NULL pointers); PSL_ECUDA if
+ * the scratch lookup or a launch fails, and, without launching anything, if a CUDA error is
+ * already pending when the call starts (that error is left for its owner to read).  Calls
+ * no allocator.  Work is queued
  * on the stream and the caller synchronises.  The first call on each device looks up the
  * scratch address, so make that first call before any stream capture.  Every call on a
  * device uses the same scratch, which keeps the previous call's contents (each call

@@ -62,11 +62,18 @@ TRACE_DTYPE = np.dtype([("step", "<u8"), ("start", "<u4"), ("kstar", "<u4"), ("a
 
 assert TRACE_DTYPE.itemsize == 128  # psl_trace_rec has no implicit padding
 
+
+class psl_alu_peak_t(ct.Structure):
+    _fields_ = [("sm_count", ct.c_int32), ("max_clock_mhz", ct.c_int32), ("blocks_per_sm", ct.c_int32),
+                ("threads_per_block", ct.c_int32), ("fadd", ct.c_double), ("alu", ct.c_double), ("mix", ct.c_double),
+                ("lookup", ct.c_double), ("ms", ct.c_double * 4)]
+
+
 EXPORTED = ["psl_config_default", "psl_init", "psl_submit", "psl_submit_ex", "psl_step", "psl_poll", "psl_best",
             "psl_release", "psl_export_state", "psl_trace", "psl_autocorr", "psl_walk_bytes", "psl_shutdown",
             "psl_last_error", "psl_profile", "psl_profile_read", "psl_autotune", "psl_set_hot_config",
             "psl_autocorr_static", "psl_inject_stall", "psl_set_max_sms",
-            "psl_best_fitness"]
+            "psl_best_fitness", "psl_transfer_bytes", "psl_set_steps_per_graph", "psl_alu_peak"]
 
 _lib = None
 
@@ -107,6 +114,9 @@ def lib():
             "psl_inject_stall": (ct.c_int, [P, ct.c_int64]),
             "psl_set_max_sms": (ct.c_int, [P, ct.c_int32]),
             "psl_best_fitness": (ct.c_int, [P, ct.c_int64, P, P, P, ct.c_size_t]),
+            "psl_transfer_bytes": (ct.c_int, [P, ct.POINTER(ct.c_uint64), ct.POINTER(ct.c_uint64)]),
+            "psl_set_steps_per_graph": (ct.c_int, [P, ct.c_int32]),
+            "psl_alu_peak": (ct.c_int, [ct.c_int32, P, ct.POINTER(psl_alu_peak_t)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -219,6 +229,17 @@ def psl_autocorr_static(seq_dev_ptr: int, L: int, C_dev_ptr: int, stream: int | 
         raise PslError(rc, "psl_autocorr_static failed")
 
 
+def psl_alu_peak(device: int = 0, stream: int | None = None) -> dict:
+    """Measured issue rates of the CUDA-core pipes (the neighbourhood kernel's roofline)."""
+    out = psl_alu_peak_t()
+    rc = lib().psl_alu_peak(device, stream, ct.byref(out))
+    if rc < 0:
+        raise PslError(rc, "psl_alu_peak failed")
+    d = {f: getattr(out, f) for f, _ in psl_alu_peak_t._fields_ if f != "ms"}
+    d["ms"] = list(out.ms)
+    return d
+
+
 def psl_walk_bytes(L: int, n_lmt: int = 6912, trace_cap: int = 0) -> int:
     return int(lib().psl_walk_bytes(L, n_lmt, trace_cap))
 
@@ -244,8 +265,8 @@ def _gpu_name() -> str:
         return "unknown-gpu"
 
 
-def psl_profile(ctx, enable: bool) -> None:
-    _check(ctx, lib().psl_profile(ctx, 1 if enable else 0))
+def psl_profile(ctx, enable: bool | int) -> None:
+    _check(ctx, lib().psl_profile(ctx, int(enable)))
 
 
 def psl_profile_read(ctx) -> dict:
@@ -365,8 +386,19 @@ class Context:
         """Test hook: the walk's next neighbourhood pass runs out its bounded waits."""
         _check(self.h, lib().psl_inject_stall(self.h, wid))
 
-    def profile(self, enable: bool = True) -> None:
-        psl_profile(self.h, enable)
+    def profile(self, enable: bool | int = True) -> None:
+        """True / 1: time every kernel; 2: the neighbourhood kernel only; False / 0: off."""
+        _check(self.h, lib().psl_profile(self.h, int(enable)))
+
+    def transfer_bytes(self) -> tuple[int, int]:
+        """(host->device, device->host) bytes the context has copied since it was created."""
+        a, b = ct.c_uint64(), ct.c_uint64()
+        _check(self.h, lib().psl_transfer_bytes(self.h, ct.byref(a), ct.byref(b)))
+        return int(a.value), int(b.value)
+
+    def set_steps_per_graph(self, steps: int) -> None:
+        """Steps per CUDA graph launch (0 = plain launches); captures the graph now when walks run."""
+        _check(self.h, lib().psl_set_steps_per_graph(self.h, steps))
 
     def profile_read(self) -> dict:
         return psl_profile_read(self.h)

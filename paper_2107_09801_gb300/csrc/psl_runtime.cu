@@ -151,13 +151,19 @@ struct psl_ctx {
   // CUDA graph of steps_per_graph steps over the current active set
   cudaGraphExec_t graph = nullptr;
   uint32_t graph_steps = 0;
-  // CUDA-event profile of kernel launches
-  bool prof = false;
+  int graph_prof = 0;  // profile mode the graph was captured with (its event nodes)
+  // CUDA-event profile of kernel launches: 0 off, 1 every kernel, 2 the neighbourhood kernel only
+  int prof = 0;
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
   std::vector<int> ev_kind;
   size_t ev_used = 0;
+  // event pairs recorded by the nodes of the captured graph (read after each graph launch)
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> gev;
+  std::vector<int> gev_kind;
   double prof_ms[kProfKinds] = {};
   uint64_t prof_n[kProfKinds] = {};
+  // bytes the library copied between host and device memory since creation
+  uint64_t h2d_bytes = 0, d2h_bytes = 0;
 };
 
 #define CK(call)                                                                          \
@@ -179,9 +185,29 @@ static int fail(psl_ctx *ctx, int code, const char *fmt, ...) {
   return code;
 }
 
+// Every host<->device copy of the library goes through here (on the context's stream), so
+// that the bytes moved are counted, not estimated.
+static cudaError_t xfer(psl_ctx *ctx, void *dst, const void *src, size_t bytes, cudaMemcpyKind kind) {
+  if (kind == cudaMemcpyHostToDevice) ctx->h2d_bytes += bytes;
+  if (kind == cudaMemcpyDeviceToHost) ctx->d2h_bytes += bytes;
+  return cudaMemcpyAsync(dst, src, bytes, kind, ctx->stream);
+}
+
+extern "C" int psl_transfer_bytes(psl_ctx *ctx, uint64_t *h2d, uint64_t *d2h) {
+  if (!ctx) return PSL_EINVAL;
+  if (h2d) *h2d = ctx->h2d_bytes;
+  if (d2h) *d2h = ctx->d2h_bytes;
+  return PSL_OK;
+}
+
+// Whether launches of this kind are bracketed by events in the current profile mode.
+static bool prof_wants(const psl_ctx *ctx, int kind) {
+  return ctx->prof == 1 || (ctx->prof == 2 && (kind == kPHot || kind == kPHotPlain || kind == kPGraph));
+}
+
 // Records an event pair around one launch when profiling is on.
 static cudaError_t prof_begin(psl_ctx *ctx, int kind) {
-  if (!ctx->prof) return cudaSuccess;
+  if (!prof_wants(ctx, kind)) return cudaSuccess;
   if (ctx->ev_used == ctx->ev.size()) {
     cudaEvent_t a, b;
     cudaError_t e = cudaEventCreate(&a);
@@ -194,9 +220,67 @@ static cudaError_t prof_begin(psl_ctx *ctx, int kind) {
   return cudaEventRecord(ctx->ev[ctx->ev_used].first, ctx->stream);
 }
 
-static cudaError_t prof_end(psl_ctx *ctx) {
-  if (!ctx->prof) return cudaSuccess;
+static cudaError_t prof_end(psl_ctx *ctx, int kind) {
+  if (!prof_wants(ctx, kind)) return cudaSuccess;
   return cudaEventRecord(ctx->ev[ctx->ev_used++].second, ctx->stream);
+}
+
+// Event pairs for the graph's event-record nodes, created before the capture begins.
+static cudaError_t gprof_reserve(psl_ctx *ctx, size_t pairs) {
+  while (ctx->gev.size() < pairs) {
+    cudaEvent_t a, b;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e != cudaSuccess) return e;
+    e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+      cudaEventDestroy(a);
+      return e;
+    }
+    ctx->gev.push_back({a, b});
+  }
+  ctx->gev_kind.clear();
+  return cudaSuccess;
+}
+
+// Inside a stream capture: an event pair recorded by graph nodes around one kernel
+// (external records, so that each launch of the graph timestamps them).
+static cudaError_t gprof_begin(psl_ctx *ctx, int kind) {
+  if (!prof_wants(ctx, kind)) return cudaSuccess;
+  const size_t q = ctx->gev_kind.size();
+  if (q >= ctx->gev.size()) return cudaErrorInvalidValue;  // reserved too few (not reached)
+  ctx->gev_kind.push_back(kind);
+  return cudaEventRecordWithFlags(ctx->gev[q].first, ctx->stream, cudaEventRecordExternal);
+}
+
+static cudaError_t gprof_end(psl_ctx *ctx, int kind) {
+  if (!prof_wants(ctx, kind)) return cudaSuccess;
+  return cudaEventRecordWithFlags(ctx->gev[ctx->gev_kind.size() - 1].second, ctx->stream, cudaEventRecordExternal);
+}
+
+static void gprof_clear(psl_ctx *ctx) {
+  for (auto &pr : ctx->gev) {
+    cudaEventDestroy(pr.first);
+    cudaEventDestroy(pr.second);
+  }
+  ctx->gev.clear();
+  ctx->gev_kind.clear();
+}
+
+static void drop_graph(psl_ctx *ctx) {
+  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  ctx->graph = nullptr;
+  gprof_clear(ctx);
+}
+
+// Folds the times of the last graph launch into the totals (the stream must be synchronised).
+static void gprof_collect(psl_ctx *ctx) {
+  for (size_t i = 0; i < ctx->gev_kind.size(); i++) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ctx->gev[i].first, ctx->gev[i].second) == cudaSuccess) {
+      ctx->prof_ms[ctx->gev_kind[i]] += ms;
+      ctx->prof_n[ctx->gev_kind[i]] += 1;
+    }
+  }
 }
 
 // Folds the recorded pairs into the totals (the stream must be synchronised).
@@ -212,10 +296,10 @@ static void prof_collect(psl_ctx *ctx) {
 }
 
 extern "C" int psl_profile(psl_ctx *ctx, int enable) {
-  if (!ctx) return PSL_EINVAL;
+  if (!ctx || enable < 0 || enable > 2) return PSL_EINVAL;
   CK(cudaStreamSynchronize(ctx->stream));
   prof_collect(ctx);
-  ctx->prof = enable != 0;
+  ctx->prof = enable;
   if (ctx->prof)
     for (int k = 0; k < kProfKinds; k++) ctx->prof_ms[k] = 0.0, ctx->prof_n[k] = 0;
   return PSL_OK;
@@ -345,7 +429,7 @@ extern "C" int psl_init(const psl_config *cfg_in, psl_ctx **out) {
 extern "C" void psl_shutdown(psl_ctx *ctx) {
   if (!ctx) return;
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
-  if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
+  drop_graph(ctx);
   for (auto &pr : ctx->ev) {
     cudaEventDestroy(pr.first);
     cudaEventDestroy(pr.second);
@@ -477,10 +561,7 @@ static int rebuild_active(psl_ctx *ctx) {
   const uint32_t fb = hot_flush_for(maxL);
   if (fb != ctx->hot_flush_sb) {
     ctx->hot_flush_sb = fb;
-    if (ctx->graph) {  // captured with the other kernel variant
-      cudaGraphExecDestroy(ctx->graph);
-      ctx->graph = nullptr;
-    }
+    drop_graph(ctx);  // captured with the other kernel variant
   }
   // Split every walk's k range into chunks when the neighbour blocks alone would leave
   // SMs idle (few walks, or a long walk on its own): aim for about four blocks per SM.
@@ -498,8 +579,7 @@ static int rebuild_active(psl_ctx *ctx) {
     const uint32_t units = ((h.L - 1 + unitK - 1) / unitK + ks - 1) / ks;  // chunk size in 960-k units
     h.ksplit = ks;
     h.kchunk_sb = units * kKchunkSbUnit;
-    CK(cudaMemcpyAsync((char *)(ctx->d_hdr + s) + offsetof(WalkDev, ksplit), &h.ksplit, 8, cudaMemcpyHostToDevice,
-                       ctx->stream));
+    CK(xfer(ctx, (char *)(ctx->d_hdr + s) + offsetof(WalkDev, ksplit), &h.ksplit, 8, cudaMemcpyHostToDevice));
     for (uint32_t i0 = 1; i0 <= h.N; i0 += T_)
       for (uint32_t c = 0; c < ks; c++) items.push_back(HotItem{s, i0, c, 0});
     ctx->max_chunk_apply = std::max(ctx->max_chunk_apply, h.nchunk_apply);
@@ -510,19 +590,14 @@ static int rebuild_active(psl_ctx *ctx) {
     if (ctx->d_items) cudaFree(ctx->d_items);
     ctx->items_cap = (uint32_t)std::max<size_t>(2 * items.size(), 4096);
     CK(cudaMalloc(&ctx->d_items, sizeof(HotItem) * ctx->items_cap));
-    if (ctx->graph) {  // the captured steps point at the old buffer
-      cudaGraphExecDestroy(ctx->graph);
-      ctx->graph = nullptr;
-    }
+    drop_graph(ctx);  // the captured steps point at the old buffer
   }
   ctx->nitems = (uint32_t)items.size();
   if (!items.empty())
-    CK(cudaMemcpyAsync(ctx->d_items, items.data(), sizeof(HotItem) * items.size(), cudaMemcpyHostToDevice,
-                       ctx->stream));
+    CK(xfer(ctx, ctx->d_items, items.data(), sizeof(HotItem) * items.size(), cudaMemcpyHostToDevice));
   if (!ctx->active.empty()) {
     std::copy(ctx->active.begin(), ctx->active.end(), ctx->h_pinned);
-    CK(cudaMemcpyAsync(ctx->d_active, ctx->h_pinned, sizeof(uint32_t) * ctx->active.size(),
-                       cudaMemcpyHostToDevice, ctx->stream));
+    CK(xfer(ctx, ctx->d_active, ctx->h_pinned, sizeof(uint32_t) * ctx->active.size(), cudaMemcpyHostToDevice));
   }
   Schedule sc{};
   sc.nactive = (uint32_t)ctx->active.size();
@@ -530,7 +605,7 @@ static int rebuild_active(psl_ctx *ctx) {
   sc.max_chunk_apply = ctx->max_chunk_apply;
   sc.max_chunk_rc = ctx->max_chunk_rc;
   sc.hot_next = 0;
-  CK(cudaMemcpyAsync(ctx->d_sched, &sc, sizeof sc, cudaMemcpyHostToDevice, ctx->stream));
+  CK(xfer(ctx, ctx->d_sched, &sc, sizeof sc, cudaMemcpyHostToDevice));
   CK(cudaStreamSynchronize(ctx->stream));  // h_pinned and sc are reused / temporaries
   ctx->active_dirty = false;
   return PSL_OK;
@@ -555,7 +630,7 @@ static int upload_schedule(psl_ctx *ctx, Schedule *d, uint32_t nactive, uint32_t
   sc.nactive = nactive;
   sc.max_chunk_apply = apply_chunks;
   sc.max_chunk_rc = rc_chunks;
-  CK(cudaMemcpyAsync(d, &sc, sizeof sc, cudaMemcpyHostToDevice, ctx->stream));
+  CK(xfer(ctx, d, &sc, sizeof sc, cudaMemcpyHostToDevice));
   CK(cudaStreamSynchronize(ctx->stream));
   return PSL_OK;
 }
@@ -585,11 +660,11 @@ static int admit(psl_ctx *ctx) {
     w.t_start = now_s();
     WalkDev &h = ctx->h_hdr[w.slot];
     fill_header(ctx, w, h);
-    CK(cudaMemcpyAsync(ctx->d_hdr + w.slot, &h, sizeof(WalkDev), cudaMemcpyHostToDevice, ctx->stream));
+    CK(xfer(ctx, ctx->d_hdr + w.slot, &h, sizeof(WalkDev), cudaMemcpyHostToDevice));
     if (!w.init_seq.empty()) {
       std::vector<uint32_t> words;
       pack_pm1(w.init_seq.data(), w.p.L, words);
-      CK(cudaMemcpyAsync(h.bits, words.data(), words.size() * 4, cudaMemcpyHostToDevice, ctx->stream));
+      CK(xfer(ctx, h.bits, words.data(), words.size() * 4, cudaMemcpyHostToDevice));
       CK(cudaStreamSynchronize(ctx->stream));  // words is a temporary
     }
     fresh.push_back((uint32_t)w.slot);
@@ -598,8 +673,7 @@ static int admit(psl_ctx *ctx) {
     it = ctx->queue.erase(it);
   }
   if (fresh.empty()) return PSL_OK;
-  CK(cudaMemcpyAsync(ctx->d_list_aux, fresh.data(), sizeof(uint32_t) * fresh.size(), cudaMemcpyHostToDevice,
-                     ctx->stream));
+  CK(xfer(ctx, ctx->d_list_aux, fresh.data(), sizeof(uint32_t) * fresh.size(), cudaMemcpyHostToDevice));
   int rc = upload_schedule(ctx, ctx->d_sched + 1, (uint32_t)fresh.size(), maxchunk, 1);
   if (rc) return rc;
   LaunchCtx c = launch_ctx(ctx, ctx->d_list_aux, ctx->d_sched + 1);
@@ -610,7 +684,7 @@ static int admit(psl_ctx *ctx) {
   if (e == cudaSuccess) e = launch_autocorr(c);
   if (e == cudaSuccess) e = launch_start_init(c);
   if (e == cudaSuccess) e = launch_apply(c);
-  if (e == cudaSuccess) e = prof_end(ctx);
+  if (e == cudaSuccess) e = prof_end(ctx, kPInit);
   if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
   if (e == cudaSuccess) prof_collect(ctx);
   if (e != cudaSuccess) return fail(ctx, PSL_ECUDA, "walk initialisation: %s", cudaGetErrorString(e));
@@ -624,7 +698,7 @@ static int refresh_headers(psl_ctx *ctx) {
   for (uint32_t s : ctx->active) top = std::max(top, s + 1);
   std::vector<WalkDev> tmp(top);
   if (top) {
-    CK(cudaMemcpyAsync(tmp.data(), ctx->d_hdr, sizeof(WalkDev) * top, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(xfer(ctx, tmp.data(), ctx->d_hdr, sizeof(WalkDev) * top, cudaMemcpyDeviceToHost));
     CK(cudaStreamSynchronize(ctx->stream));
     for (uint32_t s : ctx->active) ctx->h_hdr[s] = tmp[s];
   }
@@ -648,17 +722,47 @@ static int refresh_headers(psl_ctx *ctx) {
   return PSL_OK;
 }
 
-static cudaError_t enqueue_batched_step(psl_ctx *ctx, const LaunchCtx &c, bool timed) {
+// One step of the batched form.  Outside a capture each kernel may be bracketed by events
+// on the stream; inside a capture (captured = true) by event-record nodes of the graph.
+static cudaError_t enqueue_batched_step(psl_ctx *ctx, const LaunchCtx &c, bool captured) {
   cudaError_t (*fns[5])(const LaunchCtx &) = {launch_hot_batched, launch_select, launch_recheck, launch_decide,
                                                launch_apply};
   const int kinds[5] = {kPHot, kPSelect, kPRecheck, kPDecide, kPApply};
   for (int q = 0; q < 5; q++) {
-    cudaError_t e = timed ? prof_begin(ctx, kinds[q]) : cudaSuccess;
+    cudaError_t e = captured ? gprof_begin(ctx, kinds[q]) : prof_begin(ctx, kinds[q]);
     if (e == cudaSuccess) e = fns[q](c);
-    if (e == cudaSuccess && timed) e = prof_end(ctx);
+    if (e == cudaSuccess) e = captured ? gprof_end(ctx, kinds[q]) : prof_end(ctx, kinds[q]);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
+}
+
+// Captures steps_per_graph steps over the context's device schedule into one CUDA graph,
+// with event-record nodes around the kernels that the current profile mode times.
+static int capture_graph(psl_ctx *ctx) {
+  drop_graph(ctx);
+  const uint32_t G = (uint32_t)ctx->cfg.steps_per_graph;
+  LaunchCtx c = launch_ctx(ctx, ctx->d_active, ctx->d_sched);
+  if (ctx->prof) CK(gprof_reserve(ctx, (size_t)G * 5));
+  cudaGraph_t g;
+  CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+  cudaError_t e = cudaSuccess;
+  for (uint32_t t = 0; t < G && e == cudaSuccess; t++) e = enqueue_batched_step(ctx, c, true);
+  cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+  if (e != cudaSuccess || e2 != cudaSuccess) {
+    gprof_clear(ctx);
+    return fail(ctx, PSL_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
+  }
+  e = cudaGraphInstantiate(&ctx->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    ctx->graph = nullptr;
+    gprof_clear(ctx);
+    return fail(ctx, PSL_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
+  }
+  ctx->graph_steps = G;
+  ctx->graph_prof = ctx->prof;
+  return PSL_OK;
 }
 
 static int run_batched(psl_ctx *ctx, uint32_t steps) {
@@ -666,34 +770,41 @@ static int run_batched(psl_ctx *ctx, uint32_t steps) {
   LaunchCtx c = launch_ctx(ctx, ctx->d_active, ctx->d_sched);
   const uint32_t G = (uint32_t)ctx->cfg.steps_per_graph;
   uint32_t done = 0;
-  if (G > 0) {
-    if (!ctx->graph || ctx->graph_steps != G) {
-      if (ctx->graph) cudaGraphExecDestroy(ctx->graph);
-      ctx->graph = nullptr;
-      cudaGraph_t g;
-      CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-      cudaError_t e = cudaSuccess;
-      for (uint32_t t = 0; t < G && e == cudaSuccess; t++) e = enqueue_batched_step(ctx, c, false);
-      cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
-      if (e != cudaSuccess || e2 != cudaSuccess)
-        return fail(ctx, PSL_ECUDA, "graph capture: %s", cudaGetErrorString(e != cudaSuccess ? e : e2));
-      e = cudaGraphInstantiate(&ctx->graph, g, 0);
-      cudaGraphDestroy(g);
-      if (e != cudaSuccess) return fail(ctx, PSL_ECUDA, "graph instantiate: %s", cudaGetErrorString(e));
-      ctx->graph_steps = G;
+  if (G > 0 && steps >= G) {
+    if (!ctx->graph || ctx->graph_steps != G || ctx->graph_prof != ctx->prof) {
+      int rc = capture_graph(ctx);
+      if (rc) return rc;
     }
     while (steps - done >= G) {
       CK(prof_begin(ctx, kPGraph));
       CK(cudaGraphLaunch(ctx->graph, ctx->stream));
-      CK(prof_end(ctx));
+      CK(prof_end(ctx, kPGraph));
+      if (!ctx->gev_kind.empty()) {  // the next launch re-records the graph's events: read them now
+        CK(cudaStreamSynchronize(ctx->stream));
+        gprof_collect(ctx);
+      }
       done += G;
     }
   }
   for (; done < steps; done++) {
-    cudaError_t e = enqueue_batched_step(ctx, c, true);
+    cudaError_t e = enqueue_batched_step(ctx, c, false);
     if (e != cudaSuccess) return fail(ctx, PSL_ECUDA, "step launch: %s", cudaGetErrorString(e));
   }
   return PSL_OK;
+}
+
+extern "C" int psl_set_steps_per_graph(psl_ctx *ctx, int32_t steps) {
+  if (!ctx || steps < 0 || ctx->cfg.form != PSL_FORM_BATCHED) return PSL_EINVAL;
+  CK(cudaSetDevice(ctx->cfg.device));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->cfg.steps_per_graph = steps;
+  drop_graph(ctx);
+  if (steps == 0) return PSL_OK;
+  int rc = admit(ctx);
+  if (rc) return rc;
+  if (ctx->active_dirty && (rc = rebuild_active(ctx))) return rc;
+  if (ctx->active.empty()) return PSL_OK;  // captured at the first step that runs walks
+  return capture_graph(ctx);
 }
 
 // Host-side selection of the plain form: the same rule as k_select.
@@ -739,23 +850,23 @@ static int run_plain(psl_ctx *ctx, uint32_t steps) {
   for (uint32_t s : ctx->active) {
     WalkDev *dh = ctx->d_hdr + s;
     uint32_t list_host = s;
-    CK(cudaMemcpyAsync(ctx->d_list_aux, &list_host, sizeof(uint32_t), cudaMemcpyHostToDevice, ctx->stream));
+    CK(xfer(ctx, ctx->d_list_aux, &list_host, sizeof(uint32_t), cudaMemcpyHostToDevice));
     int rc = upload_schedule(ctx, ctx->d_sched + 2, 1, ctx->h_hdr[s].nchunk_apply, ctx->h_hdr[s].nchunk_rc);
     if (rc) return rc;
     LaunchCtx c = launch_ctx(ctx, ctx->d_list_aux, ctx->d_sched + 2);
     for (uint32_t t = 0; t < steps; t++) {
       WalkDev h;
-      CK(cudaMemcpyAsync(&h, dh, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(xfer(ctx, &h, dh, sizeof h, cudaMemcpyDeviceToHost));
       CK(cudaStreamSynchronize(ctx->stream));
       if (h.status != kRunning) break;
       CK(prof_begin(ctx, kPHotPlain));
       cudaError_t e = launch_hot_plain(dh, h.N, ctx->stream);
       if (e != cudaSuccess) return fail(ctx, PSL_ECUDA, "plain kernel: %s", cudaGetErrorString(e));
-      CK(prof_end(ctx));
+      CK(prof_end(ctx, kPHotPlain));
       score.resize(h.N);
       pslj.resize(h.N);
-      CK(cudaMemcpyAsync(score.data(), h.score, 4 * h.N, cudaMemcpyDeviceToHost, ctx->stream));
-      CK(cudaMemcpyAsync(pslj.data(), h.pslj, 4 * h.N, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(xfer(ctx, score.data(), h.score, 4 * h.N, cudaMemcpyDeviceToHost));
+      CK(xfer(ctx, pslj.data(), h.pslj, 4 * h.N, cudaMemcpyDeviceToHost));
       CK(cudaStreamSynchronize(ctx->stream));
       float m;
       double B;
@@ -764,21 +875,21 @@ static int run_plain(psl_ctx *ctx, uint32_t steps) {
       host_select(h, score, pslj, cand, &m, &B, &wp, &wi);
       const uint32_t n = (uint32_t)cand.size();
       const float bf = (float)B;
-      CK(cudaMemcpyAsync(h.cand, cand.data(), 4 * n, cudaMemcpyHostToDevice, ctx->stream));
-      CK(cudaMemcpyAsync((char *)dh + offsetof(WalkDev, ncand), &n, 4, cudaMemcpyHostToDevice, ctx->stream));
-      CK(cudaMemcpyAsync((char *)dh + offsetof(WalkDev, score_min), &m, 4, cudaMemcpyHostToDevice, ctx->stream));
-      CK(cudaMemcpyAsync((char *)dh + offsetof(WalkDev, bound), &bf, 4, cudaMemcpyHostToDevice, ctx->stream));
-      CK(cudaMemcpyAsync((char *)dh + offsetof(WalkDev, win_psl), &wp, 4, cudaMemcpyHostToDevice, ctx->stream));
-      CK(cudaMemcpyAsync((char *)dh + offsetof(WalkDev, win_psl_i), &wi, 4, cudaMemcpyHostToDevice, ctx->stream));
+      CK(xfer(ctx, h.cand, cand.data(), 4 * n, cudaMemcpyHostToDevice));
+      CK(xfer(ctx, (char *)dh + offsetof(WalkDev, ncand), &n, 4, cudaMemcpyHostToDevice));
+      CK(xfer(ctx, (char *)dh + offsetof(WalkDev, score_min), &m, 4, cudaMemcpyHostToDevice));
+      CK(xfer(ctx, (char *)dh + offsetof(WalkDev, bound), &bf, 4, cudaMemcpyHostToDevice));
+      CK(xfer(ctx, (char *)dh + offsetof(WalkDev, win_psl), &wp, 4, cudaMemcpyHostToDevice));
+      CK(xfer(ctx, (char *)dh + offsetof(WalkDev, win_psl_i), &wi, 4, cudaMemcpyHostToDevice));
       CK(prof_begin(ctx, kPRecheck));
       e = launch_recheck(c);
-      if (e == cudaSuccess) e = prof_end(ctx);
+      if (e == cudaSuccess) e = prof_end(ctx, kPRecheck);
       if (e == cudaSuccess) e = prof_begin(ctx, kPDecide);
       if (e == cudaSuccess) e = launch_decide(c);
-      if (e == cudaSuccess) e = prof_end(ctx);
+      if (e == cudaSuccess) e = prof_end(ctx, kPDecide);
       if (e == cudaSuccess) e = prof_begin(ctx, kPApply);
       if (e == cudaSuccess) e = launch_apply(c);
-      if (e == cudaSuccess) e = prof_end(ctx);
+      if (e == cudaSuccess) e = prof_end(ctx, kPApply);
       if (e != cudaSuccess) return fail(ctx, PSL_ECUDA, "plain step: %s", cudaGetErrorString(e));
       CK(cudaStreamSynchronize(ctx->stream));  // host buffers above are reused next step
       prof_collect(ctx);
@@ -903,7 +1014,7 @@ extern "C" int psl_poll(psl_ctx *ctx, int64_t id, psl_status *out) {
 
 static int download_pm1(psl_ctx *ctx, const uint32_t *dbits, uint32_t L, int8_t *out) {
   std::vector<uint32_t> words((L + 31) / 32);
-  CK(cudaMemcpyAsync(words.data(), dbits, words.size() * 4, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(xfer(ctx, words.data(), dbits, words.size() * 4, cudaMemcpyDeviceToHost));
   CK(cudaStreamSynchronize(ctx->stream));
   for (uint32_t i = 0; i < L; i++) out[i] = ((words[i >> 5] >> (i & 31)) & 1u) ? -1 : 1;
   return PSL_OK;
@@ -965,7 +1076,7 @@ extern "C" int psl_export_state(psl_ctx *ctx, int64_t id, psl_walk_state *st, in
   const uint32_t L = w->p.L;
   if ((pivot || local_best || sol_best || C) && cap < L) return fail(ctx, PSL_EINVAL, "cap < L");
   WalkDev h;
-  CK(cudaMemcpyAsync(&h, ctx->d_hdr + w->slot, sizeof h, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(xfer(ctx, &h, ctx->d_hdr + w->slot, sizeof h, cudaMemcpyDeviceToHost));
   CK(cudaStreamSynchronize(ctx->stream));
   if (st) {
     std::memset(st, 0, sizeof *st);
@@ -988,7 +1099,7 @@ extern "C" int psl_export_state(psl_ctx *ctx, int64_t id, psl_walk_state *st, in
   if (local_best && (rc = download_pm1(ctx, h.bits_local, L, local_best))) return rc;
   if (sol_best && (rc = download_pm1(ctx, h.bits_best, L, sol_best))) return rc;
   if (C) {
-    CK(cudaMemcpyAsync(C, h.C, (size_t)L * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(xfer(ctx, C, h.C, (size_t)L * 4, cudaMemcpyDeviceToHost));
     CK(cudaStreamSynchronize(ctx->stream));
   }
   return PSL_OK;
@@ -1003,7 +1114,7 @@ extern "C" int psl_trace(psl_ctx *ctx, int64_t id, psl_trace_rec *out, size_t ca
   const WalkDev &h = ctx->h_hdr[w->slot];
   const uint64_t n = std::min<uint64_t>(std::min<uint64_t>(h.moves, h.trace_cap), cap);
   if (n) {
-    CK(cudaMemcpyAsync(out, h.trace, n * sizeof(TraceRec), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(xfer(ctx, out, h.trace, n * sizeof(TraceRec), cudaMemcpyDeviceToHost));
     CK(cudaStreamSynchronize(ctx->stream));
   }
   return (int)n;
@@ -1101,10 +1212,7 @@ extern "C" int psl_autotune(psl_ctx *ctx, int reps) {
   cudaEventDestroy(b);
   ctx->cfg.hot_threads = best_t;
   ctx->cfg.hot_tile_sb = best_sb;
-  if (ctx->graph) {  // captured with another kernel variant
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
+  drop_graph(ctx);  // captured with another kernel variant
   if ((rc = rebuild_active(ctx))) return rc;
   return best_t | (best_sb << 16);
 }
@@ -1115,10 +1223,7 @@ extern "C" int psl_set_hot_config(psl_ctx *ctx, int32_t threads, int32_t tile_sb
   ctx->cfg.hot_threads = threads;
   ctx->cfg.hot_tile_sb = tile_sb;
   ctx->active_dirty = true;  // the block list depends on the block size
-  if (ctx->graph) {          // captured with another kernel variant
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
+  drop_graph(ctx);  // captured with another kernel variant
   return PSL_OK;
 }
 
@@ -1129,10 +1234,7 @@ extern "C" int psl_set_max_sms(psl_ctx *ctx, int32_t max_sms) {
   ctx->sm_count = n;
   ctx->cfg.max_sms = max_sms;
   ctx->active_dirty = true;  // the k split of each walk depends on the SM count
-  if (ctx->graph) {          // captured with the old grid sizes
-    cudaGraphExecDestroy(ctx->graph);
-    ctx->graph = nullptr;
-  }
+  drop_graph(ctx);  // captured with the old grid sizes
   return (int)n;
 }
 
@@ -1142,8 +1244,7 @@ extern "C" int psl_inject_stall(psl_ctx *ctx, int64_t id) {
   if (!w) return PSL_ENOENT;
   if (w->slot < 0) return PSL_EBUSY;
   const uint32_t one = 1;
-  CK(cudaMemcpyAsync((char *)(ctx->d_hdr + w->slot) + offsetof(WalkDev, inject_stall), &one, 4,
-                     cudaMemcpyHostToDevice, ctx->stream));
+  CK(xfer(ctx, (char *)(ctx->d_hdr + w->slot) + offsetof(WalkDev, inject_stall), &one, 4, cudaMemcpyHostToDevice));
   CK(cudaStreamSynchronize(ctx->stream));
   return PSL_OK;
 }

@@ -63,6 +63,9 @@ __global__ void k_static_autocorr(const uint32_t *scratch, uint32_t L, int32_t *
 
 extern "C" int psl_autocorr_static(const int8_t *seq_dev, uint32_t L, int32_t *C_dev, void *stream) {
   if (!seq_dev || !C_dev || L < 1 || L > kStaticMaxL) return PSL_EINVAL;
+  // an error left pending by the caller's own earlier work is not this call's to report
+  // or to clear: refuse to launch and leave it in place
+  if (cudaPeekAtLastError() != cudaSuccess) return PSL_ECUDA;
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return PSL_ECUDA;
   void *scratch = nullptr;
@@ -83,6 +86,7 @@ extern "C" int psl_autocorr_static(const int8_t *seq_dev, uint32_t L, int32_t *C
   cudaStream_t s = (cudaStream_t)stream;
   const uint32_t words = (L + 31) / 32 + 2 * kStaticGuard;
   k_static_pack<<<(words + 255) / 256, 256, 0, s>>>((uint32_t *)scratch, seq_dev, L);
+  if (cudaGetLastError() != cudaSuccess) return PSL_ECUDA;
   k_static_autocorr<<<(L + 255) / 256, 256, 0, s>>>((const uint32_t *)scratch, L, C_dev);
   return cudaGetLastError() == cudaSuccess ? PSL_OK : PSL_ECUDA;
 }

@@ -188,9 +188,25 @@ def test_continuous_admission_matches_alone(P):
 
 
 # ------------------------------------------------------------------------------------------------
-# full sizes, in the launch configuration the benchmark times, checked on sampled outputs
+# full sizes, in the launch configuration the benchmark times: every walk's final state
+# recomputed from scratch, and the last decision of some walks over their whole window
 # ------------------------------------------------------------------------------------------------
-def _check_full_size(P, wl, steps, n_check, full_window=False, sample=48):
+def _check_walk_state(ctx, wid, st=None):
+    """C_k of the pivot by the FFT route (Eq. 2), PSL (Eq. 3), exact F (Eq. 4) and the best
+    sequence's PSL recomputed from scratch; returns the exported state."""
+    st = st if st is not None else ctx.export_state(wid)
+    C = fft_autocorr(st["pivot"])
+    assert np.array_equal(st["C"].astype(np.int64), C), wid
+    assert st["psl"] == int(np.abs(C[1:]).max()), wid
+    Fx, _, _ = O.fitness(st["C"], st["alpha"])
+    assert st["F"] == Fx, wid
+    psl_b, sol = ctx.best(wid)
+    assert psl_b == st["psl_best"] and np.array_equal(sol, st["sol_best"]), wid
+    assert int(np.abs(fft_autocorr(sol)[1:]).max()) == psl_b, wid
+    return st
+
+
+def _check_full_size(P, wl, steps, n_check, every_walk=True):
     specs = list(wl.walks)
     with P.Context(arena_bytes=int(1.3 * sum(P.psl_walk_bytes(s.L, s.n_lmt, steps) for s in specs)) + (1 << 28),
                    max_walks=len(specs)) as ctx:
@@ -206,39 +222,34 @@ def _check_full_size(P, wl, steps, n_check, full_window=False, sample=48):
         for q in check:
             spec, wid = specs[q], ids[q]
             tr = ctx.trace(wid, steps)
-            st = ctx.export_state(wid)
-            s = st["pivot"]
-            C = fft_autocorr(s)
-            assert np.array_equal(st["C"].astype(np.int64), C)                 # C_k of the pivot (Eq. 2)
-            assert st["psl"] == int(np.abs(C[1:]).max())                      # PSL (Eq. 3)
-            Fx, _, _ = O.fitness(st["C"], st["alpha"])
-            assert st["F"] == Fx                                              # exact F (Eq. 4)
-            # the last decision: k* minimises the exact F over the window (first in scan order)
+            assert len(tr) == steps and ctx.poll(wid)["state"] == P.PSL_DONE
+            _check_walk_state(ctx, wid)
+            # the last decision over the whole window: k* minimises the exact F (first in scan
+            # order), and the window's first minimum PSL is the one the GPU reports
             p = pre[q]
             last = tr[-1]
             L, N = spec.L, spec.N
             assert last["start"] == p["start"]
-            window = [(p["start"] + i) % L for i in range(1, N + 1)]
-            if full_window:
-                js = window
-            else:
-                js = sorted(set(rng.choice(window, size=min(sample, N), replace=False).tolist()) | {int(last["kstar"])})
+            js = [(p["start"] + i) % L for i in range(1, N + 1)]
             vals, psls = parallel_eval(p["pivot"], p["C"], p["alpha"], js)
-            pos = {j: n for n, j in enumerate(window)}
-            kv = vals[js.index(int(last["kstar"]))]
-            assert kv == limbs32_to_int(last["value_exact"])
-            for j, v in zip(js, vals):
-                assert v > kv or (v == kv and pos[j] >= pos[int(last["kstar"])]), (q, j)
-            if full_window and last["win_psl"] != 2**31 - 1:
-                assert last["win_psl"] == psls.min()
-            # best-PSL sequence: its PSL recomputed from scratch is psl_best
-            psl_b, sol = ctx.best(wid)
-            assert psl_b == st["psl_best"] == tr[-1]["psl_best"]
-            assert int(np.abs(fft_autocorr(sol)[1:]).max()) == psl_b
+            best = min(range(N), key=lambda n: (vals[n], n))
+            assert int(last["kstar"]) == js[best], (q, int(last["kstar"]), js[best])
+            assert limbs32_to_int(last["value_exact"]) == vals[best]
+            pmin = int(psls.min())
+            if last["win_psl"] != 2**31 - 1:
+                assert last["win_psl"] == pmin and last["win_psl_j"] == js[int(np.argmin(psls))]
+            else:
+                assert pmin >= p["psl_best"]   # skipped only when no neighbour can beat psl_best
+            assert last["psl_best"] == min(p["psl_best"], pmin)
+        if every_walk:
+            # every walk of the batch: its whole state after the run, from scratch
+            for q, wid in enumerate(ids):
+                st = _check_walk_state(ctx, wid)
+                assert st["moves"] == steps and ctx.poll(wid)["state"] == P.PSL_DONE, q
 
 
 def test_full_size_L16383_x4096(P):
-    _check_full_size(P, W.batch_16383(), steps=2, n_check=2, full_window=True)
+    _check_full_size(P, W.batch_16383(), steps=2, n_check=3)
 
 
 def test_full_size_L131071_x1024(P):
@@ -246,7 +257,7 @@ def test_full_size_L131071_x1024(P):
 
 
 def test_full_size_L1048575_x148(P):
-    _check_full_size(P, W.batch_1048575(), steps=1 + 1, n_check=1, sample=24)
+    _check_full_size(P, W.batch_1048575(), steps=2, n_check=1)
 
 
 # whole budgets of the workloads on a few walks (phase switches included): the final pivot's
@@ -260,7 +271,28 @@ def test_full_budget_L131071_x2(P):
 
 
 def test_full_budget_L1048575_x1(P):
-    _check_full_size(P, W.batch_1048575(walks=1), steps=200, n_check=1, sample=24)
+    _check_full_size(P, W.batch_1048575(walks=1), steps=200, n_check=1)
+
+
+# ------------------------------------------------------------------------------------------------
+# many exact ties: more certified candidates than one re-check pass holds (the overflow path)
+# ------------------------------------------------------------------------------------------------
+@pytest.mark.parametrize("form", ["batched", "plain"])
+def test_candidate_overflow_matches_oracle(P, form):
+    """From the all-ones sequence with alpha = 1 almost every neighbour of the first window
+    has the same exact F (the flip changes every C_k = L - k by the same amount), so the
+    certified set far exceeds 64 candidates; later steps and a phase switch to alpha = 4
+    follow.  L = 40000 spreads each re-check over three k-chunks."""
+    specs = [W.WalkSpec(L=255, seed=1, alpha1=1, alpha2=4, n_lmt=255, ls_lmt=3, flip_lmt=5, budget=25),
+             W.WalkSpec(L=1023, seed=2, alpha1=1, alpha2=1, n_lmt=1023, ls_lmt=2000, budget=12),
+             W.WalkSpec(L=40000, seed=3, alpha1=1, alpha2=2, n_lmt=6912, ls_lmt=1, flip_lmt=3, budget=5)]
+    inits = [np.ones(s.L, dtype=np.int8) for s in specs]
+    res = run_gpu(P, specs, form=form, init_seqs=inits)
+    for spec, s0, (tr, st, _, _) in zip(specs, inits, res):
+        assert int(tr["ncand"].max()) > 64, (spec.L, tr["ncand"])
+        w = oracle_walk(spec, s0=s0)
+        compare_traces(tr, w.run(spec.budget), f"{form} L={spec.L}")
+        compare_final_state(st, w)
 
 
 # ------------------------------------------------------------------------------------------------
@@ -487,3 +519,50 @@ def test_merit_factor_workload_sampled_walks(P):
             w = oracle_walk(specs[r])
             w.run(specs[r].budget)
             assert got[r][0] == w.F_best and np.array_equal(got[r][1], w.fbest_seq), r
+
+
+# ------------------------------------------------------------------------------------------------
+# measurement hooks: events inside captured graphs, counted copies, the pipe microbenchmarks
+# ------------------------------------------------------------------------------------------------
+def test_graph_profile_and_transfer_counts(P):
+    specs = W.small_specs(seed=31, count=4, L_choices=(255, 1023, 4095))
+    specs = [W.with_budget(s, 20) for s in specs]
+    with P.Context(arena_bytes=ARENA, max_walks=8) as ctx:
+        ids = [submit_spec(ctx, s) for s in specs]
+        h0, d0 = ctx.transfer_bytes()
+        ctx.step(2)
+        ctx.profile(2)                   # neighbourhood kernel only, from event nodes of the graph
+        ctx.set_steps_per_graph(4)       # captured now: no step runs
+        assert ctx.poll(ids[0])["moves"] == 2
+        ctx.step(8)
+        pr = ctx.profile_read()
+        assert pr["hot"][0] == 8 and pr["hot"][1] > 0 and pr["graph"][0] == 2
+        assert pr["select"][0] == 0 and pr["apply"][0] == 0
+        ctx.profile(1)                   # every kernel: the graph is captured again
+        ctx.step(4)
+        pr = ctx.profile_read()
+        assert all(pr[k][0] == 4 for k in ("hot", "select", "recheck", "decide", "apply")), pr
+        ctx.profile(0)
+        ctx.set_steps_per_graph(0)
+        ctx.run()
+        h1, d1 = ctx.transfer_bytes()
+        assert h1 > h0 and d1 > d0
+        psl, seq = ctx.best(ids[0])
+        h2, d2 = ctx.transfer_bytes()
+        assert h2 == h1 and d2 - d1 == 4 * ((specs[0].L + 31) // 32)
+        for i, s in zip(ids, specs):
+            w = oracle_walk(s)
+            compare_traces(ctx.trace(i, s.budget), w.run(s.budget), f"L={s.L}")
+            compare_final_state(ctx.export_state(i), w)
+
+
+def test_alu_peak_microbenchmark(P):
+    import torch
+    from paper_2107_09801_gb300 import binding as B
+    pk = B.psl_alu_peak(0, torch.cuda.current_stream().cuda_stream)
+    assert pk["sm_count"] == torch.cuda.get_device_properties(0).multi_processor_count
+    per_clk = {k: pk[k] / (pk["sm_count"] * pk["max_clock_mhz"] * 1e6) for k in ("fadd", "alu", "mix", "lookup")}
+    # lane-ops per SM per clock at the top clock: no pipe can exceed 4 schedulers x 32 lanes
+    assert all(0 < v <= 128 * 1.02 for v in per_clk.values()), per_clk
+    assert per_clk["fadd"] > 32 and per_clk["mix"] > 32 and per_clk["lookup"] > 4, per_clk
+    print("lane-ops (lookups) per SM per clock:", per_clk)
