@@ -102,6 +102,8 @@ typedef struct {
   int32_t topk;             /* FP32-ranked neighbours re-scored exactly besides the certified set (1..16) */
   const int8_t *init_seq;   /* optional host array of L values +-1 replacing Rand(L, SEED); copied */
   uint32_t trace_cap;       /* per-step records kept on the device (0 = none)        */
+  uint32_t shard_rank;      /* single-walk k-sharding (psl_shard_*): this context's rank ...          */
+  uint32_t shard_count;     /* ... of shard_count ranks; 0 or 1 = not sharded                        */
 } psl_walk_params;
 
 /* Snapshot of one walk (psl_poll). */
@@ -306,6 +308,32 @@ PSL_API int psl_autocorr_static(const int8_t *seq_dev, uint32_t L, int32_t *C_de
  * while every other walk and the context carry on.  Nothing faults and nothing is left in
  * flight.  PSL_ENOENT / PSL_EBUSY if the walk is unknown or not yet admitted. */
 PSL_API int psl_inject_stall(psl_ctx *ctx, int64_t id);
+
+/* Single-walk k-sharding over several ranks (one context per rank, typically one GPU each):
+ * the parallel evaluation of Sec. 3 split over k, the sum of Eq. 4 being a sum over k.  A walk
+ * submitted with shard_count = R > 1 (2 <= R <= min(16, ceil((L-1)/960)); the context must
+ * hold no other walk) keeps its whole state on every rank, but each rank scores and
+ * re-checks only the k-chunks c with c % R == shard_rank.  One step of Algorithm 1 is:
+ *   n = psl_shard_score(ctx, id, parts, cap)      this rank's partial FP32 scores, [ksplit][N],
+ *                                                  other ranks' chunks zero
+ *   parts <- sum over ranks of parts              (exact: every entry has one non-zero term)
+ *   m = psl_shard_select(ctx, id, parts, rc, cap)  selection on the full scores (identical on
+ *                                                  every rank), then this rank's exact re-check
+ *                                                  partials of the candidates, m uint32 words
+ *                                                  (other ranks' chunks zero)
+ *   rc <- sum over ranks of rc, word by word      (exact for the same reason: no carries)
+ *   psl_shard_decide(ctx, id, rc, m)              the exact decision and the O(L) update, the
+ *                                                  same on every rank; returns PSL_RUNNING or
+ *                                                  PSL_DONE
+ * The walk's trajectory equals that of the same walk run unsharded.  psl_step refuses a
+ * context that holds a sharded walk (PSL_ESTATE).  psl_shard_layout gives the sizes: ksplit
+ * (k-chunks), N (window) and the most re-check words a step can produce.  Errors:
+ * PSL_ENOENT (unknown id), PSL_EINVAL (not sharded, cap too small), PSL_ESTATE (the walk is
+ * done or failed), PSL_ETIMEOUT (a bounded device wait ran out; the walk failed). */
+PSL_API int psl_shard_layout(psl_ctx *ctx, int64_t id, uint32_t *ksplit, uint32_t *N, uint32_t *rc_words_max);
+PSL_API int psl_shard_score(psl_ctx *ctx, int64_t id, float *parts, size_t cap);
+PSL_API int psl_shard_select(psl_ctx *ctx, int64_t id, const float *parts, uint32_t *rc_parts, size_t cap);
+PSL_API int psl_shard_decide(psl_ctx *ctx, int64_t id, const uint32_t *rc_parts, size_t words);
 
 /* Destroys the context and frees its device memory.  NULL is ignored. */
 PSL_API void psl_shutdown(psl_ctx *ctx);

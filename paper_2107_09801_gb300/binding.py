@@ -32,7 +32,8 @@ class psl_config(ct.Structure):
 class psl_walk_params(ct.Structure):
     _fields_ = [("L", ct.c_uint32), ("seed", ct.c_uint64), ("alpha1", ct.c_int32), ("alpha2", ct.c_int32),
                 ("budget", ct.c_uint64), ("n_lmt", ct.c_int32), ("ls_lmt", ct.c_int32), ("flip_lmt", ct.c_int32),
-                ("topk", ct.c_int32), ("init_seq", ct.c_void_p), ("trace_cap", ct.c_uint32)]
+                ("topk", ct.c_int32), ("init_seq", ct.c_void_p), ("trace_cap", ct.c_uint32),
+                ("shard_rank", ct.c_uint32), ("shard_count", ct.c_uint32)]
 
 
 class psl_status(ct.Structure):
@@ -73,7 +74,8 @@ EXPORTED = ["psl_config_default", "psl_init", "psl_submit", "psl_submit_ex", "ps
             "psl_release", "psl_export_state", "psl_trace", "psl_autocorr", "psl_walk_bytes", "psl_shutdown",
             "psl_last_error", "psl_profile", "psl_profile_read", "psl_autotune", "psl_set_hot_config",
             "psl_autocorr_static", "psl_inject_stall", "psl_set_max_sms",
-            "psl_best_fitness", "psl_transfer_bytes", "psl_set_steps_per_graph", "psl_alu_peak"]
+            "psl_best_fitness", "psl_transfer_bytes", "psl_set_steps_per_graph", "psl_alu_peak",
+            "psl_shard_layout", "psl_shard_score", "psl_shard_select", "psl_shard_decide"]
 
 _lib = None
 
@@ -117,6 +119,11 @@ def lib():
             "psl_transfer_bytes": (ct.c_int, [P, ct.POINTER(ct.c_uint64), ct.POINTER(ct.c_uint64)]),
             "psl_set_steps_per_graph": (ct.c_int, [P, ct.c_int32]),
             "psl_alu_peak": (ct.c_int, [ct.c_int32, P, ct.POINTER(psl_alu_peak_t)]),
+            "psl_shard_layout": (ct.c_int, [P, ct.c_int64, ct.POINTER(ct.c_uint32), ct.POINTER(ct.c_uint32),
+                                            ct.POINTER(ct.c_uint32)]),
+            "psl_shard_score": (ct.c_int, [P, ct.c_int64, P, ct.c_size_t]),
+            "psl_shard_select": (ct.c_int, [P, ct.c_int64, P, P, ct.c_size_t]),
+            "psl_shard_decide": (ct.c_int, [P, ct.c_int64, P, ct.c_size_t]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -306,10 +313,10 @@ class Context:
         return wid
 
     def submit_ex(self, L, seed, alpha1=4, alpha2=13, budget=2000, *, n_lmt=0, ls_lmt=-1, flip_lmt=0, topk=1,
-                  init_seq=None, trace_cap=0) -> int:
+                  init_seq=None, trace_cap=0, shard_rank=0, shard_count=0) -> int:
         seq = None if init_seq is None else np.ascontiguousarray(init_seq, dtype=np.int8)
         p = psl_walk_params(L, seed, alpha1, alpha2, budget, n_lmt, ls_lmt, flip_lmt, topk,
-                            None if seq is None else seq.ctypes.data, trace_cap)
+                            None if seq is None else seq.ctypes.data, trace_cap, shard_rank, shard_count)
         wid = psl_submit_ex(self.h, p)
         self.L_of[wid] = L
         return wid
@@ -381,6 +388,34 @@ class Context:
         """Sizes the persistent kernels for max_sms SMs from the next step on (0 = all);
         returns the SM count in use."""
         return _check(self.h, lib().psl_set_max_sms(self.h, max_sms))
+
+    # ---- single-walk k-sharding (one step = score, exchange, select, exchange, decide) ----
+    def shard_layout(self, wid: int) -> tuple[int, int, int]:
+        """(k-chunks, window size N, most re-check words of a step) of a sharded walk."""
+        a, b, c = ct.c_uint32(), ct.c_uint32(), ct.c_uint32()
+        _check(self.h, lib().psl_shard_layout(self.h, wid, ct.byref(a), ct.byref(b), ct.byref(c)))
+        return int(a.value), int(b.value), int(c.value)
+
+    def shard_score(self, wid: int) -> np.ndarray:
+        """This rank's partial FP32 scores, float32 [ksplit, N]; other ranks' chunks are zero."""
+        ks, n, _ = self.shard_layout(wid)
+        parts = np.zeros((ks, n), dtype=np.float32)
+        _check(self.h, lib().psl_shard_score(self.h, wid, parts.ctypes.data, parts.size))
+        return parts
+
+    def shard_select(self, wid: int, parts: np.ndarray) -> np.ndarray:
+        """Selection on the summed scores, then this rank's exact re-check words (uint32)."""
+        parts = np.ascontiguousarray(parts, dtype=np.float32)
+        _, _, cap = self.shard_layout(wid)
+        out = np.zeros(cap, dtype=np.uint32)
+        m = _check(self.h, lib().psl_shard_select(self.h, wid, parts.ctypes.data, out.ctypes.data, cap))
+        return out[:m]
+
+    def shard_decide(self, wid: int, rc_words: np.ndarray) -> int:
+        """The exact decision and update from the summed re-check words; returns the walk state."""
+        rc_words = np.ascontiguousarray(rc_words, dtype=np.uint32)
+        return _check(self.h, lib().psl_shard_decide(self.h, wid, rc_words.ctypes.data if rc_words.size else None,
+                                                      rc_words.size))
 
     def inject_stall(self, wid: int) -> None:
         """Test hook: the walk's next neighbourhood pass runs out its bounded waits."""

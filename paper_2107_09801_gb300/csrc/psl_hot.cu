@@ -508,7 +508,7 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem *items, Sche
   if (!live) return true;
   if (W.ksplit > 1) {
     W.score_part[(size_t)it.kc * N + (i - 1)] = hi + lo;
-    if (it.kc != 0) return true;
+    if (it.kc != W.kc_psl) return true;
   } else {
     W.score[i - 1] = hi + lo;
   }
@@ -547,41 +547,107 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_hot_batched(WalkDev *hdr, con
 }
 
 // ------------------------------------------------------------------------------------
-// neighbourhood score, plain form: one thread per neighbour, every term accumulated
-// on its own (the execution model of the paper's GPU solver)
+// neighbourhood score, plain form: one thread per neighbour, every term accumulated on its
+// own (the execution model of the paper's GPU solver: one walk, one neighbour per core).
+// Blocks of 64 threads spread the window over the SMs; each block stages the per-k values
+// of 1024 shifts at a time into shared memory with a TMA bulk copy (double-buffered), so
+// every term reads its (Tp4, Tm4, Tp2, Tm2) by a broadcast shared load; for each run of 32
+// shifts a lane forms four disjoint bit masks (both partners +4 / -4, one partner +2 / -2)
+// and every term adds the one value its bit selects, without a branch.
 // ------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_hot_plain(WalkDev *hdrp) {
-  const WalkDev &W = *hdrp;
+constexpr int kPlainThreads = 64;
+constexpr int kPlainTileK = 1024;
+
+size_t hot_plain_smem() { return 2 * (size_t)kPlainTileK * 16; }
+
+// TMA bulk copy of the per-k values of shifts 1 + 1024 tile .. (those below L) into staging
+// buffer tile & 1, signalling that buffer's mbarrier.
+__device__ __forceinline__ void plain_stage_copy(uint32_t stage_s, uint32_t mbar_s, int tile, const float4 *T, int L) {
+  const int kt0 = 1 + tile * kPlainTileK;
+  const uint32_t bytes = 16u * (uint32_t)min(kPlainTileK, L - kt0);
+  const uint32_t mb = mbar_s + 8u * (uint32_t)(tile & 1);
+  fence_proxy_async();
+  mbar_expect_tx(mb, bytes);
+  tma_load_1d(stage_s + (uint32_t)(tile & 1) * (kPlainTileK * 16), T + kt0, bytes, mb);
+}
+
+__global__ void __launch_bounds__(kPlainThreads, 1) k_hot_plain(WalkDev *hdrp) {
+  extern __shared__ __align__(128) float4 pstage[];  // 2 x kPlainTileK staged per-k values
+  __shared__ __align__(8) uint64_t s_mbar[2];
+  __shared__ int s_kmax, s_timeout;
+  WalkDev &W = *hdrp;
   const int L = (int)W.L, N = (int)W.N;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;
-  if (i > N) return;
-  const uint32_t *bits = W.bits;
-  const float4 *T = W.T;
-  const int j = (int)(((uint64_t)W.start + (uint64_t)i) % (uint64_t)L);
+  const int i = blockIdx.x * blockDim.x + threadIdx.x + 1;  // window position, 1-based
+  // lanes past the end of the window shadow the last neighbour (their sums are discarded)
+  const int j = (int)(((uint64_t)W.start + (uint64_t)min(i, N)) % (uint64_t)L);
+  const uint32_t *__restrict__ bits = W.bits;
   const int kin = min(j, L - 1 - j), kout = max(j, L - 1 - j);
   const bool plus_side = j < L - 1 - j;
   const uint32_t M = getbit(bits, j) ? 0xffffffffu : 0u;
   const int cap_u = 32 * (int)W.nw;
-  float hi = 0.f, lo = 0.f, blk = 0.f;
-  for (int ka = 1; ka <= kout; ka += kSbK) {
-    const uint32_t U = window32(bits, min(j + ka, cap_u)) ^ M;
-    const uint32_t V = __brev(window32(bits, max(j - ka - 31, -64))) ^ M;
-    const int kend = min(ka + kSbK - 1, kout);
-    for (int k = ka; k <= kend; k++) {
-      const int t = k - ka;
-      const float4 tv = T[k];
-      const uint32_t u = (U >> t) & 1u, v = (V >> t) & 1u;
-      if (k <= kin) {
-        if (u & v)
-          blk += tv.x;
-        else if (!(u | v))
-          blk += tv.y;
-      } else {
-        blk += (plus_side ? u : v) ? tv.z : tv.w;
-      }
-    }
-    flush_block(hi, lo, blk);
+  const uint32_t mbar_s = (uint32_t)__cvta_generic_to_shared(s_mbar);
+  const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(pstage);
+  if (threadIdx.x == 0) {
+    s_kmax = 0;
+    s_timeout = 0;
+    mbar_init(mbar_s, 1);
+    mbar_init(mbar_s + 8, 1);
+    fence_mbar_init();
   }
+  __syncthreads();
+  atomicMax(&s_kmax, kout);
+  __syncthreads();
+  const int ntiles = (s_kmax + kPlainTileK - 1) / kPlainTileK;
+  if (threadIdx.x == 0 && ntiles > 0) plain_stage_copy(stage_s, mbar_s, 0, W.T, L);
+  float hi = 0.f, lo = 0.f;
+  int issued = ntiles > 0 ? 1 : 0;  // copies issued so far (tiles 0 .. issued-1)
+  for (int tile = 0; tile < ntiles; tile++) {
+    const int kt0 = 1 + tile * kPlainTileK;
+    __syncthreads();  // the buffer the next copy overwrites is no longer read
+    if (s_timeout) break;  // one reading for the whole block
+    if (tile + 1 < ntiles) {
+      if (threadIdx.x == 0) plain_stage_copy(stage_s, mbar_s, tile + 1, W.T, L);
+      issued = tile + 2;
+    }
+    if (!mbar_wait_bounded(mbar_s + 8u * (tile & 1), (tile >> 1) & 1)) s_timeout = 1;
+    const float4 *Ts = pstage + (tile & 1) * kPlainTileK;
+    const int kend = min(kout, kt0 + kPlainTileK - 1);
+    for (int k0 = kt0; k0 <= kend; k0 += 32) {
+      const uint32_t U = window32_ro(bits, min(j + k0, cap_u)) ^ M;          // bit t: s_j s_{j+k0+t} = -1
+      const uint32_t V = __brev(window32_ro(bits, max(j - k0 - 31, -64))) ^ M;  // bit t: s_j s_{j-k0-t} = -1
+      const int nb = min(32, max(0, kin - k0 + 1)), nl = min(32, kout - k0 + 1);
+      const uint32_t both = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
+      const uint32_t live = nl >= 32 ? 0xffffffffu : ((1u << nl) - 1u);
+      const uint32_t one = live & ~both;
+      const uint32_t P = plus_side ? U : V;
+      const uint32_t W1 = U & V & both, W0 = ~(U | V) & both, Ep = P & one, Em = ~P & one;
+      const float4 *Tk = Ts + (k0 - kt0);
+      float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+      for (int t = 0; t < 32; t += 2) {
+        const float4 x = Tk[t], y = Tk[t + 1];  // shifts past the tile's copy are masked out
+        a0 += ((W1 >> t) & 1u) ? x.x : (((W0 >> t) & 1u) ? x.y : (((Ep >> t) & 1u) ? x.z : (((Em >> t) & 1u) ? x.w : 0.f)));
+        a1 += ((W1 >> (t + 1)) & 1u) ? y.x
+                                      : (((W0 >> (t + 1)) & 1u) ? y.y
+                                                                : (((Ep >> (t + 1)) & 1u) ? y.z
+                                                                                          : (((Em >> (t + 1)) & 1u) ? y.w : 0.f)));
+      }
+      float blk = a0 + a1;
+      flush_block(hi, lo, blk);
+    }
+  }
+  __syncthreads();
+  if (s_timeout) {
+    // a staged copy never arrived: give the copies still outstanding one more bounded wait,
+    // then mark the walk failed instead of using its scores
+    if (threadIdx.x == 0) {
+      for (int q = max(0, issued - 2); q < issued; q++) mbar_wait_bounded(mbar_s + 8u * (q & 1), (q >> 1) & 1);
+      W.error = (uint32_t)-5;  // PSL_ETIMEOUT of the library header
+      W.status = kError;
+    }
+    return;
+  }
+  if (i > N) return;
   W.score[i - 1] = hi + lo;
   int pj = INT_MAX;
   if (W.ktau_on) pj = neighbour_psl(W, W.ktau, (int)W.nktau, j, L, M ? -1 : 1, W.psl - 8, 0);
@@ -612,6 +678,10 @@ bool hot_config_supported(uint32_t threads, uint32_t tile_sb) {
 uint32_t hot_flush_for(uint32_t maxL) { return maxL >= 4096u ? 8u : 4u; }
 
 cudaError_t prepare_hot_kernels() {
+  {
+    cudaError_t e = cudaFuncSetAttribute(k_hot_plain, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hot_plain_smem());
+    if (e != cudaSuccess) return e;
+  }
   for (uint32_t t : {128u, 256u, 512u})
     for (uint32_t sb : {16u, 32u})
       for (uint32_t fb : {4u, 8u}) {
@@ -635,7 +705,7 @@ cudaError_t launch_hot_batched(const LaunchCtx &c) {
 }
 
 cudaError_t launch_hot_plain(WalkDev *hdr_one, uint32_t N, cudaStream_t s) {
-  k_hot_plain<<<(N + 127) / 128, 128, 0, s>>>(hdr_one);
+  k_hot_plain<<<(N + kPlainThreads - 1) / kPlainThreads, kPlainThreads, hot_plain_smem(), s>>>(hdr_one);
   return cudaGetLastError();
 }
 

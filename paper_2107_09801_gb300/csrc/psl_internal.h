@@ -52,6 +52,8 @@ struct WalkDev {
   uint64_t seed, budget;
   uint32_t nchunk_apply, nchunk_rc, trace_cap, has_init_seq;
   uint32_t track_fbest, pad_static;  // keep the lowest-F pivot (alpha1 == alpha2: one objective)
+  uint32_t shard_rank, shard_count;  // k-sharding of one walk over ranks: this rank scores and re-checks the
+                                     // k-chunks c with c % shard_count == shard_rank (count <= 1: all of them)
   uint32_t *bits, *bits_local, *bits_best;  // logical word 0 (guards before and after)
   uint32_t *bits_fbest;                     // lowest-F pivot (when track_fbest)
   int32_t *C, *C_local;
@@ -82,6 +84,7 @@ struct WalkDev {
   uint32_t arrive;
   uint32_t alpha_next;
   uint32_t ksplit, kchunk_sb;  // k-chunks of the neighbourhood kernel and their size (super-blocks)
+  uint32_t kc_psl, pad_kc;     // the k-chunk whose blocks also compute the neighbours' exact PSL
   uint32_t inject_stall;       // test hook: the next neighbourhood pass waits on copies never issued
   float score_min, bound;
   uint32_t flips[kMaxFlips];

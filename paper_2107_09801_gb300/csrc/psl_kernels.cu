@@ -713,6 +713,7 @@ __global__ void __launch_bounds__(256) k_recheck(WalkDev *hdr, const uint32_t *a
     WalkDev &W = hdr[active[v / nch]];
     const uint32_t chunk = v % nch;
     if (W.status != kRunning || chunk >= W.nchunk_rc) continue;  // uniform over the block
+    if (W.shard_count > 1 && chunk % W.shard_count != W.shard_rank) continue;  // another rank's chunk
     const uint32_t nslots = min(W.ncand, (uint32_t)kQcap);
     for (uint32_t qslot = 0; qslot < nslots; qslot++) {
       __syncthreads();

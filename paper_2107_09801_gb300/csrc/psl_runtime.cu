@@ -456,6 +456,17 @@ static int check_params(psl_ctx *ctx, psl_walk_params &p) {
   if (p.flip_lmt > kMaxFlips) return fail(ctx, PSL_EINVAL, "flip_lmt > %d", kMaxFlips);
   if (p.topk <= 0) p.topk = 1;
   if (p.topk > 16) return fail(ctx, PSL_EINVAL, "topk > 16");
+  if (p.shard_count > 1) {
+    const uint32_t unitK = kKchunkSbUnit * kSbK;
+    const uint32_t max_split = std::max<uint32_t>(1u, (p.L - 1 + unitK - 1) / unitK);
+    if (p.shard_rank >= p.shard_count || p.shard_count > std::min<uint32_t>(kKsplitMax, max_split))
+      return fail(ctx, PSL_EINVAL, "shard_rank %u / shard_count %u: need rank < count <= min(16, ceil((L-1)/960))",
+                  p.shard_rank, p.shard_count);
+    if (ctx->cfg.form != PSL_FORM_BATCHED) return fail(ctx, PSL_EINVAL, "a sharded walk needs the batched form");
+    if (!ctx->walks.empty()) return fail(ctx, PSL_EINVAL, "a sharded walk needs a context of its own");
+  } else if (!ctx->walks.empty() && ctx->walks.begin()->second.p.shard_count > 1) {
+    return fail(ctx, PSL_EINVAL, "the context holds a sharded walk");
+  }
   return PSL_OK;
 }
 
@@ -533,6 +544,9 @@ static void fill_header(psl_ctx *ctx, HostWalk &w, WalkDev &h) {
   h.score_part = (float *)(base + w.lay.score_part);
   h.ksplit = 1;
   h.kchunk_sb = kKchunkSbUnit;
+  h.kc_psl = 0;
+  h.shard_rank = p.shard_count > 1 ? p.shard_rank : 0u;
+  h.shard_count = p.shard_count > 1 ? p.shard_count : 1u;
   h.pslj = (int32_t *)(base + w.lay.pslj);
   h.ktau = (int2 *)(base + w.lay.ktau);
   h.cand = (uint32_t *)(base + w.lay.cand);
@@ -575,13 +589,19 @@ static int rebuild_active(psl_ctx *ctx) {
     WalkDev &h = ctx->h_hdr[s];
     const uint32_t unitK = kKchunkSbUnit * kSbK;
     const uint32_t max_split = std::max<uint32_t>(1u, (h.L - 1 + unitK - 1) / unitK);
-    const uint32_t ks = std::min(want, max_split);
+    uint32_t ks = std::min(want, max_split);
+    const uint32_t R = h.shard_count;
+    if (R > 1)  // a sharded walk: the same chunks on every rank whatever its SM count, the same number per rank
+      ks = std::min<uint32_t>(kKsplitMax, max_split) / R * R;
     const uint32_t units = ((h.L - 1 + unitK - 1) / unitK + ks - 1) / ks;  // chunk size in 960-k units
     h.ksplit = ks;
     h.kchunk_sb = units * kKchunkSbUnit;
-    CK(xfer(ctx, (char *)(ctx->d_hdr + s) + offsetof(WalkDev, ksplit), &h.ksplit, 8, cudaMemcpyHostToDevice));
+    h.kc_psl = R > 1 ? h.shard_rank : 0u;  // the rank's first chunk also computes the neighbours' PSL
+    static_assert(offsetof(WalkDev, kc_psl) == offsetof(WalkDev, ksplit) + 8, "ksplit, kchunk_sb, kc_psl adjacent");
+    CK(xfer(ctx, (char *)(ctx->d_hdr + s) + offsetof(WalkDev, ksplit), &h.ksplit, 16, cudaMemcpyHostToDevice));
     for (uint32_t i0 = 1; i0 <= h.N; i0 += T_)
-      for (uint32_t c = 0; c < ks; c++) items.push_back(HotItem{s, i0, c, 0});
+      for (uint32_t c = 0; c < ks; c++)
+        if (R <= 1 || c % R == h.shard_rank) items.push_back(HotItem{s, i0, c, 0});
     ctx->max_chunk_apply = std::max(ctx->max_chunk_apply, h.nchunk_apply);
     ctx->max_chunk_rc = std::max(ctx->max_chunk_rc, h.nchunk_rc);
   }
@@ -865,9 +885,12 @@ static int run_plain(psl_ctx *ctx, uint32_t steps) {
       CK(prof_end(ctx, kPHotPlain));
       score.resize(h.N);
       pslj.resize(h.N);
+      uint32_t status_after = kRunning;
       CK(xfer(ctx, score.data(), h.score, 4 * h.N, cudaMemcpyDeviceToHost));
       CK(xfer(ctx, pslj.data(), h.pslj, 4 * h.N, cudaMemcpyDeviceToHost));
+      CK(xfer(ctx, &status_after, (char *)dh + offsetof(WalkDev, status), 4, cudaMemcpyDeviceToHost));
       CK(cudaStreamSynchronize(ctx->stream));
+      if (status_after != kRunning) break;  // a bounded wait of the kernel ran out: the walk failed
       float m;
       double B;
       int32_t wp;
@@ -904,8 +927,14 @@ struct NvtxRange {
   ~NvtxRange() { nvtxRangePop(); }
 };
 
+static bool holds_sharded_walk(const psl_ctx *ctx) {
+  return !ctx->walks.empty() && ctx->walks.begin()->second.p.shard_count > 1;
+}
+
 extern "C" int psl_step(psl_ctx *ctx, uint32_t max_moves) {
   if (!ctx) return PSL_EINVAL;
+  if (holds_sharded_walk(ctx))
+    return fail(ctx, PSL_ESTATE, "a sharded walk steps through psl_shard_score / _select / _decide");
   NvtxRange r_step("psl_step");
   CK(cudaSetDevice(ctx->cfg.device));
   int rc;
@@ -1247,4 +1276,125 @@ extern "C" int psl_inject_stall(psl_ctx *ctx, int64_t id) {
   CK(xfer(ctx, (char *)(ctx->d_hdr + w->slot) + offsetof(WalkDev, inject_stall), &one, 4, cudaMemcpyHostToDevice));
   CK(cudaStreamSynchronize(ctx->stream));
   return PSL_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// single-walk k-sharding: one step split into the rank's share of the work and two
+// exchanges that the caller performs (sums over ranks of zero-filled arrays)
+// ---------------------------------------------------------------------------------
+// The sharded walk of the context, admitted and listed; nullptr after fail().
+static HostWalk *shard_walk(psl_ctx *ctx, int64_t id, int *rc) {
+  *rc = PSL_OK;
+  HostWalk *w = find(ctx, id);
+  if (!w) {
+    *rc = PSL_ENOENT;
+    return nullptr;
+  }
+  if (w->p.shard_count < 2) {
+    *rc = fail(ctx, PSL_EINVAL, "walk %lld is not sharded", (long long)id);
+    return nullptr;
+  }
+  if (cudaSetDevice(ctx->cfg.device) != cudaSuccess) {
+    *rc = fail(ctx, PSL_ECUDA, "cudaSetDevice failed");
+    return nullptr;
+  }
+  if ((*rc = admit(ctx))) return nullptr;
+  if (ctx->active_dirty && (*rc = rebuild_active(ctx))) return nullptr;
+  if (w->state != PSL_RUNNING) {
+    *rc = fail(ctx, w->state == PSL_QUEUED ? PSL_ENOMEM : PSL_ESTATE, "walk %lld is not running", (long long)id);
+    return nullptr;
+  }
+  return w;
+}
+
+extern "C" int psl_shard_layout(psl_ctx *ctx, int64_t id, uint32_t *ksplit, uint32_t *N, uint32_t *rc_words_max) {
+  if (!ctx) return PSL_EINVAL;
+  HostWalk *w = find(ctx, id);
+  if (!w) return PSL_ENOENT;
+  if (w->p.shard_count < 2) return fail(ctx, PSL_EINVAL, "walk %lld is not sharded", (long long)id);
+  if (w->slot < 0) {  // queued: admit it, so that its chunks are known
+    int rc;
+    if (!shard_walk(ctx, id, &rc)) return rc;
+  }
+  const WalkDev &h = ctx->h_hdr[w->slot];
+  if (ksplit) *ksplit = h.ksplit;
+  if (N) *N = h.N;
+  if (rc_words_max) *rc_words_max = ((uint32_t)kQcap * h.nchunk_rc + h.N) * kWideLimbs;
+  return PSL_OK;
+}
+
+extern "C" int psl_shard_score(psl_ctx *ctx, int64_t id, float *parts, size_t cap) {
+  if (!ctx || !parts) return PSL_EINVAL;
+  int rc;
+  HostWalk *w = shard_walk(ctx, id, &rc);
+  if (!w) return rc;
+  const WalkDev &h = ctx->h_hdr[w->slot];
+  const size_t n = (size_t)h.ksplit * h.N;
+  if (cap < n) return fail(ctx, PSL_EINVAL, "cap %zu < ksplit x N = %zu", cap, n);
+  LaunchCtx c = launch_ctx(ctx, ctx->d_active, ctx->d_sched);
+  // other ranks' chunks stay zero, so that the sum over ranks of every rank's array is exact
+  CK(cudaMemsetAsync(h.score_part, 0, n * 4, ctx->stream));
+  CK(cudaMemsetAsync(&ctx->d_sched->hot_next, 0, 4, ctx->stream));
+  CK(prof_begin(ctx, kPHot));
+  CK(launch_hot_batched(c));
+  CK(prof_end(ctx, kPHot));
+  CK(xfer(ctx, parts, h.score_part, n * 4, cudaMemcpyDeviceToHost));
+  uint32_t status = kRunning;
+  CK(xfer(ctx, &status, (char *)(ctx->d_hdr + w->slot) + offsetof(WalkDev, status), 4, cudaMemcpyDeviceToHost));
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_collect(ctx);
+  if (status != kRunning) {
+    refresh_headers(ctx);
+    return fail(ctx, PSL_ETIMEOUT, "a bounded wait of the neighbourhood kernel ran out");
+  }
+  return (int)n;
+}
+
+extern "C" int psl_shard_select(psl_ctx *ctx, int64_t id, const float *parts, uint32_t *rc_parts, size_t cap) {
+  if (!ctx || !parts || !rc_parts) return PSL_EINVAL;
+  int rc;
+  HostWalk *w = shard_walk(ctx, id, &rc);
+  if (!w) return rc;
+  const WalkDev &h = ctx->h_hdr[w->slot];
+  const size_t n = (size_t)h.ksplit * h.N;
+  LaunchCtx c = launch_ctx(ctx, ctx->d_active, ctx->d_sched);
+  CK(xfer(ctx, h.score_part, parts, n * 4, cudaMemcpyHostToDevice));
+  CK(prof_begin(ctx, kPSelect));
+  CK(launch_select(c));
+  CK(prof_end(ctx, kPSelect));
+  uint32_t ncand = 0;
+  CK(xfer(ctx, &ncand, (char *)(ctx->d_hdr + w->slot) + offsetof(WalkDev, ncand), 4, cudaMemcpyDeviceToHost));
+  CK(cudaStreamSynchronize(ctx->stream));
+  const size_t slots = ncand <= (uint32_t)kQcap ? (size_t)ncand * h.nchunk_rc
+                                                 : (size_t)kQcap * h.nchunk_rc + (ncand - kQcap);
+  const size_t words = slots * kWideLimbs;
+  if (cap < words) return fail(ctx, PSL_EINVAL, "cap %zu < %zu re-check words", cap, words);
+  // other ranks' chunks stay zero: the limbs of each slot come from one rank only
+  CK(cudaMemsetAsync(h.rc_part, 0, words * 4, ctx->stream));
+  CK(prof_begin(ctx, kPRecheck));
+  CK(launch_recheck(c));
+  CK(prof_end(ctx, kPRecheck));
+  CK(xfer(ctx, rc_parts, h.rc_part, words * 4, cudaMemcpyDeviceToHost));
+  CK(cudaStreamSynchronize(ctx->stream));
+  prof_collect(ctx);
+  return (int)words;
+}
+
+extern "C" int psl_shard_decide(psl_ctx *ctx, int64_t id, const uint32_t *rc_parts, size_t words) {
+  if (!ctx || (!rc_parts && words)) return PSL_EINVAL;
+  int rc;
+  HostWalk *w = shard_walk(ctx, id, &rc);
+  if (!w) return rc;
+  const WalkDev &h = ctx->h_hdr[w->slot];
+  if (words > ((size_t)kQcap * h.nchunk_rc + h.N) * kWideLimbs) return fail(ctx, PSL_EINVAL, "too many words");
+  LaunchCtx c = launch_ctx(ctx, ctx->d_active, ctx->d_sched);
+  if (words) CK(xfer(ctx, h.rc_part, rc_parts, words * 4, cudaMemcpyHostToDevice));
+  CK(prof_begin(ctx, kPDecide));
+  CK(launch_decide(c));
+  CK(prof_end(ctx, kPDecide));
+  CK(prof_begin(ctx, kPApply));
+  CK(launch_apply(c));
+  CK(prof_end(ctx, kPApply));
+  if ((rc = refresh_headers(ctx))) return rc;
+  return w->state;
 }
