@@ -459,7 +459,9 @@ def run_ours(args):
     roof = hot_roofline(len(specs) * N, L, hot_avg_ms, peak, mhz, stored_counters("k_hot_batched", wl.name))
     roof["hot_launches_timed"] = n_hot
     kernels = {k: {"launches": n, "avg_ms": (ms_ / n if n else 0.0)} for k, (n, ms_) in breakdown.items() if n}
-    launches = args.steps * 5     # hot, select, recheck, decide, apply per step
+    # kernels per step: the neighbourhood score, then either one fused kernel (short walks) or
+    # select, re-check, decide and the two update passes (ordinary moves; initialisation/switch)
+    launches = args.steps * (2 if breakdown.get("tail", (0, 0.0))[0] else 6)
 
     # plain form: one walk per launch, one thread per neighbour, host-side selection
     plain = None

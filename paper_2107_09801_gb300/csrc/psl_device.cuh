@@ -122,6 +122,53 @@ __device__ __forceinline__ void add_pow(uint32_t (&acc)[kWideLimbs], uint32_t c)
   wide_add(acc, p);
 }
 
+// The same on NL-limb accumulators (NL = 4 or 8), for values whose bound is known: the
+// caller guarantees c^A and every partial sum fit in 32 NL bits.
+template <int NL>
+__device__ __forceinline__ void wide_add_n(uint32_t (&a)[NL], const uint32_t (&b)[NL]) {
+  static_assert(NL == 4 || NL == 8, "4 or 8 limbs");
+  if constexpr (NL == 4) {
+    asm("add.cc.u32 %0, %0, %4;\n\t"
+        "addc.cc.u32 %1, %1, %5;\n\t"
+        "addc.cc.u32 %2, %2, %6;\n\t"
+        "addc.u32 %3, %3, %7;"
+        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3])
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]));
+  } else {
+    asm("add.cc.u32 %0, %0, %8;\n\t"
+        "addc.cc.u32 %1, %1, %9;\n\t"
+        "addc.cc.u32 %2, %2, %10;\n\t"
+        "addc.cc.u32 %3, %3, %11;\n\t"
+        "addc.cc.u32 %4, %4, %12;\n\t"
+        "addc.cc.u32 %5, %5, %13;\n\t"
+        "addc.cc.u32 %6, %6, %14;\n\t"
+        "addc.u32 %7, %7, %15;"
+        : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7])
+        : "r"(b[0]), "r"(b[1]), "r"(b[2]), "r"(b[3]), "r"(b[4]), "r"(b[5]), "r"(b[6]), "r"(b[7]));
+  }
+}
+
+template <int A, int NL>
+__device__ __forceinline__ void add_pow_n(uint32_t (&acc)[NL], uint32_t c) {
+  uint32_t p[NL];
+  p[0] = c;
+#pragma unroll
+  for (int i = 1; i < NL; i++) p[i] = 0;
+#pragma unroll
+  for (int t = 2; t <= A; t++) {
+    uint64_t carry = 0;
+#pragma unroll
+    for (int i = 0; i < NL; i++) {
+      if (i < (21 * t + 31) / 32) {
+        const uint64_t v = (uint64_t)p[i] * c + carry;
+        p[i] = (uint32_t)v;
+        carry = v >> 32;
+      }
+    }
+  }
+  wide_add_n<NL>(acc, p);
+}
+
 __device__ __forceinline__ void add_pow_rt(uint32_t (&acc)[kWideLimbs], uint32_t c, uint32_t alpha) {
   switch (alpha) {
     case 1: add_pow<1>(acc, c); break;

@@ -29,12 +29,24 @@ namespace psl {
 // super-block, so the common case runs without per-group tests.  Block sums of at most 48
 // values are flushed into a compensated (hi, lo) pair.
 // ------------------------------------------------------------------------------------
-constexpr int kSbFloats = 576;           // 6 groups x 3 tables x 32 entries
-constexpr int kSbBytes = kSbFloats * 4;  // 2304 bytes = 18 x 128
+// Table layout of one super-block.  The short-walk variants (MB, "masked boundaries") add two
+// tables per group, Ep[b] = sum_{q in b} Tp2_q and Em[b] = sum_{q in b} Tm2_q, so that a group
+// where lanes of a warp sit in different regions is scored by four lookups of masked
+// indices (the two-partner shifts in W1 and W0, the one-partner shifts in Ep and Em)
+// instead of term by term: 640 bytes per group, 3840 per super-block (30 x 128).
+template <bool MB>
+struct TabLayout {
+  static constexpr int GS = MB ? 640 : 384;  // bytes per group: W1, W0, E (, Ep, Em)
+  static constexpr int SBB = 6 * GS;         // bytes per super-block: 18 or 30 x 128
+  static constexpr int SBF = SBB / 4;
+};
 
 // tables (rounded up to a 128-byte boundary inside the allocation), two TMA staging
 // buffers of the tile's per-k values, and a few ints of block-wide state
-size_t hot_batched_smem(uint32_t tile_sb) { return (size_t)tile_sb * kSbBytes + 2 * (size_t)tile_sb * kSbK * 16 + 256; }
+size_t hot_batched_smem(uint32_t tile_sb, bool masked) {
+  return (size_t)tile_sb * (masked ? TabLayout<true>::SBB : TabLayout<false>::SBB) + 2 * (size_t)tile_sb * kSbK * 16 +
+         256;
+}
 
 // ---- TMA bulk copies and mbarriers (sm_90 and later) ----
 __device__ __forceinline__ void mbar_init(uint32_t mbar, uint32_t count) {
@@ -91,9 +103,11 @@ __device__ __forceinline__ uint32_t window32_ro(const uint32_t *__restrict__ bit
 // tables of group q of super-block sb of the tile (first k of the group: kg)
 // (the tile's per-k values come from the shared staging buffer Ts, entry kg - kt0).
 // W1/W0 are built only when some lane of the block scores a two-partner shift in the
-// super-block (need_w), E only when some lane scores a one-partner shift there (need_e).
+// super-block (need_w), E only when some lane scores a one-partner shift there (need_e),
+// Ep/Em (MB variants) only where a region boundary of some lane of the block falls (need_m).
+template <bool MB>
 __device__ __forceinline__ void build_group(float *tab, int sb, int q, const float4 *Ts, int kt0, int kg, int L,
-                                            bool need_w, bool need_e) {
+                                            bool need_w, bool need_e, bool need_m) {
   float tp4[5], tm4[5], tp2[5], tm2[5];
 #pragma unroll
   for (int t = 0; t < 5; t++) {
@@ -124,7 +138,7 @@ __device__ __forceinline__ void build_group(float *tab, int sb, int q, const flo
     hie[b] = p + tm2[4];
     hie[b + 4] = p + tp2[4];
   }
-  float *base = tab + sb * kSbFloats + q * 96;
+  float *base = tab + sb * TabLayout<MB>::SBF + q * (TabLayout<MB>::GS / 4);
   const int sw = sb & 31;
   if (need_w) {
 #pragma unroll
@@ -138,6 +152,25 @@ __device__ __forceinline__ void build_group(float *tab, int sb, int q, const flo
 #pragma unroll
     for (int b = 0; b < 32; b++) base[64 + (b ^ sw)] = loe[b & 3] + hie[b >> 2];
   }
+  if constexpr (MB) {
+    if (need_m) {
+      // subset sums of Tp2 and of Tm2, split into the low two and the high three bits as above
+      float lop[4], lom[4], hip[8], him[8];
+      lop[0] = 0.f, lop[1] = tp2[0], lop[2] = tp2[1], lop[3] = tp2[0] + tp2[1];
+      lom[0] = 0.f, lom[1] = tm2[0], lom[2] = tm2[1], lom[3] = tm2[0] + tm2[1];
+      const float p23 = tp2[2] + tp2[3], m23 = tm2[2] + tm2[3];
+      hip[0] = 0.f, hip[1] = tp2[2], hip[2] = tp2[3], hip[3] = p23;
+      hip[4] = tp2[4], hip[5] = tp2[2] + tp2[4], hip[6] = tp2[3] + tp2[4], hip[7] = p23 + tp2[4];
+      him[0] = 0.f, him[1] = tm2[2], him[2] = tm2[3], him[3] = m23;
+      him[4] = tm2[4], him[5] = tm2[2] + tm2[4], him[6] = tm2[3] + tm2[4], him[7] = m23 + tm2[4];
+#pragma unroll
+      for (int b = 0; b < 32; b++) {
+        const int lo = b & 3, hi = b >> 2;
+        base[96 + (b ^ sw)] = lo == 0 ? hip[hi] : (hi == 0 ? lop[lo] : lop[lo] + hip[hi]);
+        base[128 + (b ^ sw)] = lo == 0 ? him[hi] : (hi == 0 ? lom[lo] : lom[lo] + him[hi]);
+      }
+    }
+  }
 }
 
 // Shift range of one warp's lanes: min/max of kin and kout over its 32 neighbours.
@@ -147,19 +180,30 @@ struct WarpRange {
 
 // One group of a super-block where lanes may sit in different regions.  The choice is
 // warp-uniform: a table lookup when every lane of the warp has both partners (or every
-// lane exactly one) for all five shifts; otherwise the five terms one by one from the
+// lane exactly one) for all five shifts; otherwise, in the MB variants, four lookups of
+// indices masked to each lane's own regions, else the five terms one by one from the
 // tile's staged per-k values, each lane selecting its own case without a branch.
-template <int Q>
+template <int Q, bool MB>
 __device__ __forceinline__ void group_generic(float &a0, float &a1, uint32_t bsw, uint32_t W1, uint32_t W0,
                                               uint32_t E, uint32_t U, uint32_t V, int ka, int kin, int kout,
                                               bool plus_side, const float4 *Ts, int kt0, const WarpRange &wr) {
+  constexpr int GS = TabLayout<MB>::GS;
   const int kg = ka + 5 * Q;
   if (kg > wr.kout_hi) return;
   if (kg + 4 <= wr.kin_lo) {
-    a0 += lds_at<Q * 384>(field4<Q>(W1) ^ bsw);
-    a1 += lds_at<Q * 384 + 128>(field4<Q>(W0) ^ bsw);
+    a0 += lds_at<Q * GS>(field4<Q>(W1) ^ bsw);
+    a1 += lds_at<Q * GS + 128>(field4<Q>(W0) ^ bsw);
   } else if (kg > wr.kin_hi && kg + 4 <= wr.kout_lo) {
-    a0 += lds_at<Q * 384 + 256>(field4<Q>(E) ^ bsw);
+    a0 += lds_at<Q * GS + 256>(field4<Q>(E) ^ bsw);
+  } else if constexpr (MB) {
+    // shifts kg .. kg+nb-1 have both partners, kg+nb .. kg+nl-1 one (bits 2..6 of the index)
+    const int nb = min(5, max(0, kin - kg + 1)), nl = min(5, max(0, kout - kg + 1));
+    const uint32_t mb = ((1u << nb) - 1u) << 2;
+    const uint32_t me = (((1u << nl) - 1u) << 2) & ~mb;
+    a0 += lds_at<Q * GS>((field4<Q>(W1) & mb) ^ bsw);
+    a1 += lds_at<Q * GS + 128>((field4<Q>(W0) & mb) ^ bsw);
+    a0 += lds_at<Q * GS + 384>((field4<Q>(E) & me) ^ bsw);   // partner bit 1: delta = +2
+    a1 += lds_at<Q * GS + 512>((field4<Q>(~E) & me) ^ bsw);  // partner bit 0: delta = -2
   } else {
 #pragma unroll
     for (int t = 0; t < 5; t++) {
@@ -189,56 +233,63 @@ __device__ __forceinline__ int neighbour_psl(const WalkDev &W, const int2 *list,
   return cur;
 }
 
-// One super-block where every lane has both partners for all 30 shifts.
-__device__ __forceinline__ void sb_interior(float &a0, float &a1, const uint32_t *__restrict__ bits, int pos_u,
-                                            int pos_v, uint32_t M, uint32_t bsw) {
-  const uint32_t U = window32_ro(bits, pos_u);
-  const uint32_t V = __brev(window32_ro(bits, pos_v));
+// One super-block where every lane has both partners for all 30 shifts; wu and wv point at
+// the lane's forward and backward partner windows of the super-block's first shift.
+template <bool MB>
+__device__ __forceinline__ void sb_interior(float &a0, float &a1, const uint32_t *__restrict__ wu,
+                                            const uint32_t *__restrict__ wv, uint32_t M, uint32_t bsw) {
+  constexpr int GS = TabLayout<MB>::GS;
+  const uint32_t U = __ldg(wu);
+  const uint32_t V = __ldg(wv);
   const uint32_t W1 = (U ^ M) & (V ^ M), W0 = ~((U ^ M) | (V ^ M));
-  a0 += lds_at<0 * 384>(field4<0>(W1) ^ bsw);
-  a1 += lds_at<0 * 384 + 128>(field4<0>(W0) ^ bsw);
-  a0 += lds_at<1 * 384>(field4<1>(W1) ^ bsw);
-  a1 += lds_at<1 * 384 + 128>(field4<1>(W0) ^ bsw);
-  a0 += lds_at<2 * 384>(field4<2>(W1) ^ bsw);
-  a1 += lds_at<2 * 384 + 128>(field4<2>(W0) ^ bsw);
-  a0 += lds_at<3 * 384>(field4<3>(W1) ^ bsw);
-  a1 += lds_at<3 * 384 + 128>(field4<3>(W0) ^ bsw);
-  a0 += lds_at<4 * 384>(field4<4>(W1) ^ bsw);
-  a1 += lds_at<4 * 384 + 128>(field4<4>(W0) ^ bsw);
-  a0 += lds_at<5 * 384>(field4<5>(W1) ^ bsw);
-  a1 += lds_at<5 * 384 + 128>(field4<5>(W0) ^ bsw);
+  a0 += lds_at<0 * GS>(field4<0>(W1) ^ bsw);
+  a1 += lds_at<0 * GS + 128>(field4<0>(W0) ^ bsw);
+  a0 += lds_at<1 * GS>(field4<1>(W1) ^ bsw);
+  a1 += lds_at<1 * GS + 128>(field4<1>(W0) ^ bsw);
+  a0 += lds_at<2 * GS>(field4<2>(W1) ^ bsw);
+  a1 += lds_at<2 * GS + 128>(field4<2>(W0) ^ bsw);
+  a0 += lds_at<3 * GS>(field4<3>(W1) ^ bsw);
+  a1 += lds_at<3 * GS + 128>(field4<3>(W0) ^ bsw);
+  a0 += lds_at<4 * GS>(field4<4>(W1) ^ bsw);
+  a1 += lds_at<4 * GS + 128>(field4<4>(W0) ^ bsw);
+  a0 += lds_at<5 * GS>(field4<5>(W1) ^ bsw);
+  a1 += lds_at<5 * GS + 128>(field4<5>(W0) ^ bsw);
 }
 
-// One super-block where every lane has exactly one partner for all 30 shifts.
-__device__ __forceinline__ void sb_edge(float &a0, float &a1, const uint32_t *__restrict__ bits, int pos,
-                                        bool plus_side, uint32_t M, uint32_t bsw) {
-  const uint32_t w = window32_ro(bits, pos);
-  const uint32_t E = (plus_side ? w : __brev(w)) ^ M;
-  a0 += lds_at<0 * 384 + 256>(field4<0>(E) ^ bsw);
-  a1 += lds_at<1 * 384 + 256>(field4<1>(E) ^ bsw);
-  a0 += lds_at<2 * 384 + 256>(field4<2>(E) ^ bsw);
-  a1 += lds_at<3 * 384 + 256>(field4<3>(E) ^ bsw);
-  a0 += lds_at<4 * 384 + 256>(field4<4>(E) ^ bsw);
-  a1 += lds_at<5 * 384 + 256>(field4<5>(E) ^ bsw);
+// One super-block where every lane has exactly one partner for all 30 shifts; we points at
+// the lane's window of that partner (forward or backward) for the super-block's first shift.
+template <bool MB>
+__device__ __forceinline__ void sb_edge(float &a0, float &a1, const uint32_t *__restrict__ we, uint32_t M,
+                                        uint32_t bsw) {
+  constexpr int GS = TabLayout<MB>::GS;
+  const uint32_t E = __ldg(we) ^ M;
+  a0 += lds_at<0 * GS + 256>(field4<0>(E) ^ bsw);
+  a1 += lds_at<1 * GS + 256>(field4<1>(E) ^ bsw);
+  a0 += lds_at<2 * GS + 256>(field4<2>(E) ^ bsw);
+  a1 += lds_at<3 * GS + 256>(field4<3>(E) ^ bsw);
+  a0 += lds_at<4 * GS + 256>(field4<4>(E) ^ bsw);
+  a1 += lds_at<5 * GS + 256>(field4<5>(E) ^ bsw);
 }
 
 // One super-block where region boundaries fall inside it for some lane of the warp.
 // Partner bits outside the sequence (clamped windows) are only ever paired with a case
 // that ignores them.
-__device__ __forceinline__ void sb_generic(float &a0, float &a1, const uint32_t *__restrict__ bits,
-                                           const float4 *Ts, int kt0, int j, int ka, int kin, int kout,
-                                           bool plus_side, uint32_t M, uint32_t bsw, int cap_u,
-                                           const WarpRange &wr) {
+template <bool MB>
+__device__ __forceinline__ void sb_generic(float &a0, float &a1, const uint32_t *__restrict__ win_f,
+                                           const uint32_t *__restrict__ win_r, const float4 *Ts, int kt0, int j,
+                                           int ka, int kin, int kout, bool plus_side, uint32_t M, uint32_t bsw,
+                                           int L, const WarpRange &wr) {
   if (ka > wr.kout_hi) return;
-  const uint32_t U = window32_ro(bits, min(j + ka, cap_u)) ^ M;
-  const uint32_t V = __brev(window32_ro(bits, max(j - ka - 31, -64))) ^ M;
+  // past either end every partner bit is 0 (entries L and -1 of the windows)
+  const uint32_t U = __ldg(win_f + min(j + ka, L)) ^ M;
+  const uint32_t V = __ldg(win_r + max(j - ka, -1)) ^ M;
   const uint32_t W1 = U & V, W0 = ~(U | V), E = plus_side ? U : V;
-  group_generic<0>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
-  group_generic<1>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
-  group_generic<2>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
-  group_generic<3>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
-  group_generic<4>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
-  group_generic<5>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
+  group_generic<0, MB>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
+  group_generic<1, MB>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
+  group_generic<2, MB>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
+  group_generic<3, MB>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
+  group_generic<4, MB>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
+  group_generic<5, MB>(a0, a1, bsw, W1, W0, E, U, V, ka, kin, kout, plus_side, Ts, kt0, wr);
 }
 
 __device__ __forceinline__ void flush2(float &hi, float &lo, float &a0, float &a1) {
@@ -290,18 +341,21 @@ template <int NT, int NSB, int FB>
 __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem *items, Schedule *sched, const uint32_t item,
                                         HotPipe &pipe, uint32_t mbar_s, uint32_t *s_next) {
   static_assert(NSB <= 32, "the per-super-block swizzle assumes at most 32 super-blocks per tile");
+  constexpr bool MB = FB == 4;  // short walks: boundary groups by masked lookups
+  constexpr int SBB = TabLayout<MB>::SBB;
   extern __shared__ __align__(128) float smem_raw[];
   const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(smem_raw);
   const uint32_t tab_s = (raw_s + 127u) & ~127u;  // lookups OR a swizzle into the low 7 bits
   float *tab = smem_raw + (tab_s - raw_s) / 4;
   constexpr int kTileK = NSB * kSbK;
-  float4 *stage = reinterpret_cast<float4 *>(tab + NSB * kSbFloats);  // 2 x kTileK staged T values
-  const uint32_t stage_s = tab_s + NSB * kSbBytes;
+  float4 *stage = reinterpret_cast<float4 *>(tab + NSB * TabLayout<MB>::SBF);  // 2 x kTileK staged T values
+  const uint32_t stage_s = tab_s + NSB * SBB;
   int *s_kmax = reinterpret_cast<int *>(stage + 2 * kTileK);
   int *s_timeout = s_kmax + 1;
   int *s_kin_lo = s_kmax + 2, *s_kin_hi = s_kmax + 3;  // block-wide range of kin
   int *s_run = s_kmax + 4;                              // the walk was running when the item began
   int *s_pre = s_kmax + 5;                              // the next item's first copy is issued
+  int *s_kout_lo = s_kmax + 6;                          // block-wide minimum of kout
   const HotItem it = items[item];
   WalkDev &W = hdr[it.slot];
   // thread 0 takes the next item (copy q issued for its first tile when `prefetch`)
@@ -327,6 +381,7 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem *items, Sche
     *s_kmax = 0;
     *s_timeout = 0;
     *s_kin_lo = INT_MAX;
+    *s_kout_lo = INT_MAX;
     *s_kin_hi = 0;
     *s_run = W.status == kRunning ? 1 : 0;  // one reading for the whole block
   }
@@ -356,7 +411,8 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem *items, Sche
   const int kin = min(j, L - 1 - j), kout = max(j, L - 1 - j);
   const bool plus_side = j < L - 1 - j;
   const uint32_t M = getbit(bits, j) ? 0xffffffffu : 0u;
-  const int cap_u = 32 * (int)W.nw;
+  const uint32_t *__restrict__ win_f = W.win_f;
+  const uint32_t *__restrict__ win_r = W.win_r;
   const int w_kin_lo = __reduce_min_sync(0xffffffffu, kin);
   const int w_kin_hi = __reduce_max_sync(0xffffffffu, kin);
   const int w_kout_lo = __reduce_min_sync(0xffffffffu, kout);
@@ -365,11 +421,12 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem *items, Sche
   if ((threadIdx.x & 31) == 0) {
     atomicMax(s_kmax, w_kout_hi);
     atomicMin(s_kin_lo, w_kin_lo);
+    if (warp_live) atomicMin(s_kout_lo, w_kout_lo);
     atomicMax(s_kin_hi, w_kin_hi);
   }
   __syncthreads();
   const int kmax = *s_kmax;
-  const int blk_kin_lo = *s_kin_lo, blk_kin_hi = *s_kin_hi;
+  const int blk_kin_lo = *s_kin_lo, blk_kin_hi = *s_kin_hi, blk_kout_lo = *s_kout_lo;
   // tiles of this block: all of them, or those of its k-chunk when the k range is split
   const int tiles_per_chunk = (int)W.kchunk_sb / NSB;
   const int tile_lo = item_tile_lo<NSB>(W, it);
@@ -416,7 +473,11 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem *items, Sche
         // shifts kin < k <= kout iff ka + 29 > min kin and ka <= max kout
         const bool need_w = ka <= blk_kin_hi;
         const bool need_e = ka + kSbK - 1 > blk_kin_lo && ka <= kmax;
-        if (need_w || need_e) build_group(tab, sb, q, Ts, kt0, ka + 5 * q, L, need_w, need_e);
+        // a group straddles some lane's kin or kout only inside [min kin - 4, max kin] or
+        // [min kout - 4, max kout]
+        const bool need_m = MB && ((ka <= blk_kin_hi && ka + kSbK - 1 >= blk_kin_lo - 4) ||
+                                   (ka <= kmax && ka + kSbK - 1 >= blk_kout_lo - 4));
+        if (need_w || need_e) build_group<MB>(tab, sb, q, Ts, kt0, ka + 5 * q, L, need_w, need_e, need_m);
       }
     }
     __syncthreads();
@@ -429,55 +490,54 @@ __device__ __forceinline__ bool hot_one(WalkDev *hdr, const HotItem *items, Sche
     const int n_int = min(sb_count(w_kin_lo, kt0, kSbK - 1, NSB), n_all);
     const int e0 = max(n_int, min(n_all, sb_count(w_kin_hi, kt0, 0, NSB)));
     const int n_edge = max(e0, min(n_all, sb_count(w_kout_lo, kt0, kSbK - 1, NSB)));
-    const uint32_t bsw0 = tab_s;  // super-block sb: base + 2304 sb, swizzle sb << 2
+    const uint32_t bsw0 = tab_s;  // super-block sb: base + SBB sb, swizzle sb << 2
     int sb = 0;
     {
-      int pu = j + kt0, pv = j - kt0 - 31;
+      const uint32_t *wu = win_f + (j + kt0), *wv = win_r + (j - kt0);
       uint32_t bsw = bsw0;
       // FB super-blocks per flush: at most 6 FB additions into either accumulator
       for (; sb + FB - 1 < n_int; sb += FB) {
 #pragma unroll
-        for (int u = 0; u < FB; u++)
-          sb_interior(a0, a1, bits, pu + u * kSbK, pv - u * kSbK, M, bsw + u * (kSbBytes + 4));
+        for (int u = 0; u < FB; u++) sb_interior<MB>(a0, a1, wu + u * kSbK, wv - u * kSbK, M, bsw + u * (SBB + 4));
         flush2(hi, lo, a0, a1);
-        pu += FB * kSbK, pv -= FB * kSbK, bsw += FB * (kSbBytes + 4);
+        wu += FB * kSbK, wv -= FB * kSbK, bsw += FB * (SBB + 4);
       }
       if (sb < n_int) {
         for (; sb < n_int; sb++) {
-          sb_interior(a0, a1, bits, pu, pv, M, bsw);
-          pu += kSbK, pv -= kSbK, bsw += kSbBytes + 4;
+          sb_interior<MB>(a0, a1, wu, wv, M, bsw);
+          wu += kSbK, wv -= kSbK, bsw += SBB + 4;
         }
         flush2(hi, lo, a0, a1);
       }
     }
     const float4 *Ts = stage + (cq & 1u) * kTileK;  // this tile's per-k values, still staged
     for (; sb < e0; sb++) {
-      sb_generic(a0, a1, bits, Ts, kt0, j, kt0 + sb * kSbK, kin, kout, plus_side, M, bsw0 + sb * (kSbBytes + 4),
-                 cap_u, wr);
+      sb_generic<MB>(a0, a1, win_f, win_r, Ts, kt0, j, kt0 + sb * kSbK, kin, kout, plus_side, M,
+                     bsw0 + sb * (SBB + 4), L, wr);
       flush2(hi, lo, a0, a1);
     }
     {
       const int step = plus_side ? kSbK : -kSbK;
-      int pe = plus_side ? j + kt0 + sb * kSbK : j - kt0 - sb * kSbK - 31;
-      uint32_t bsw = bsw0 + sb * (kSbBytes + 4);
+      const uint32_t *we = plus_side ? win_f + (j + kt0 + sb * kSbK) : win_r + (j - kt0 - sb * kSbK);
+      uint32_t bsw = bsw0 + sb * (SBB + 4);
       // FB super-blocks per flush: at most 3 FB additions into either accumulator
       for (; sb + FB - 1 < n_edge; sb += FB) {
 #pragma unroll
-        for (int u = 0; u < FB; u++) sb_edge(a0, a1, bits, pe + u * step, plus_side, M, bsw + u * (kSbBytes + 4));
+        for (int u = 0; u < FB; u++) sb_edge<MB>(a0, a1, we + u * step, M, bsw + u * (SBB + 4));
         flush2(hi, lo, a0, a1);
-        pe += FB * step, bsw += FB * (kSbBytes + 4);
+        we += FB * step, bsw += FB * (SBB + 4);
       }
       if (sb < n_edge) {
         for (; sb < n_edge; sb++) {
-          sb_edge(a0, a1, bits, pe, plus_side, M, bsw);
-          pe += step, bsw += kSbBytes + 4;
+          sb_edge<MB>(a0, a1, we, M, bsw);
+          we += step, bsw += SBB + 4;
         }
         flush2(hi, lo, a0, a1);
       }
     }
     for (; sb < n_all; sb++) {
-      sb_generic(a0, a1, bits, Ts, kt0, j, kt0 + sb * kSbK, kin, kout, plus_side, M, bsw0 + sb * (kSbBytes + 4),
-                 cap_u, wr);
+      sb_generic<MB>(a0, a1, win_f, win_r, Ts, kt0, j, kt0 + sb * kSbK, kin, kout, plus_side, M,
+                     bsw0 + sb * (SBB + 4), L, wr);
       flush2(hi, lo, a0, a1);
     }
   }
@@ -535,6 +595,15 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_hot_batched(WalkDev *hdr, con
     mbar_init(mbar_s + 8, 1);
     fence_mbar_init();
     s_next = atomicAdd(&sched->hot_next, 1u);
+  }
+  if constexpr (FB == 4) {
+    // masked lookups with an empty mask read entry 0 (the empty subset) of tables that a
+    // super-block may not have built: start from zero tables, and every build writes 0
+    // there again, so entry 0 of every table always holds 0
+    extern __shared__ __align__(128) float smem_tab[];
+    const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(smem_tab);
+    float *tab = smem_tab + (((raw_s + 127u) & ~127u) - raw_s) / 4;
+    for (int q = threadIdx.x; q < NSB * TabLayout<true>::SBF; q += NT) tab[q] = 0.f;
   }
   __syncthreads();
   HotPipe pipe{0u, false};
@@ -686,10 +755,10 @@ cudaError_t prepare_hot_kernels() {
     for (uint32_t sb : {16u, 32u})
       for (uint32_t fb : {4u, 8u}) {
         HotFn f = hot_variant(t, sb, fb);
-        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hot_batched_smem(sb));
+        cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)hot_batched_smem(sb, fb == 4));
         if (e != cudaSuccess) return e;
         int nb = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, (int)t, hot_batched_smem(sb));
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, (int)t, hot_batched_smem(sb, fb == 4));
         if (e != cudaSuccess) return e;
         g_hot_blocks_per_sm[variant_index(t)][sb == 32 ? 1 : 0][fb == 8 ? 1 : 0] = (uint32_t)(nb > 0 ? nb : 1);
       }
@@ -700,7 +769,7 @@ cudaError_t launch_hot_batched(const LaunchCtx &c) {
   const uint32_t fb = c.hot_flush_sb == 4 ? 4u : 8u;
   const uint32_t per_sm = g_hot_blocks_per_sm[variant_index(c.hot_threads)][c.hot_tile_sb == 32 ? 1 : 0][fb == 8 ? 1 : 0];
   hot_variant(c.hot_threads, c.hot_tile_sb, fb)<<<per_sm * c.sm_count, c.hot_threads,
-                                                  hot_batched_smem(c.hot_tile_sb), c.stream>>>(c.hdr, c.items, c.sched);
+                                                  hot_batched_smem(c.hot_tile_sb, fb == 4), c.stream>>>(c.hdr, c.items, c.sched);
   return cudaGetLastError();
 }
 

@@ -24,6 +24,7 @@ constexpr int kApplyPartStride = 32;  // u32 per apply-chunk partial record
 constexpr int kFlushBlockAdds = 64;   // FP32 additions per lane before a compensated flush
 constexpr int kKsplitMax = 16;        // most k-chunks one neighbour's score may be split into
 constexpr int kKchunkSbUnit = 32;     // k-chunks are whole multiples of 32 super-blocks (960 k)
+constexpr int kWinGuard = 32;         // entries before index 0 and past index L-1 of the partner windows
 
 enum WalkStatus : uint32_t { kFree = 0, kRunning = 1, kDone = 2, kError = 3 };
 enum ApplyMode : uint32_t { kModeInit = 0, kModeMove = 1, kModeSwitch = 2 };
@@ -56,6 +57,10 @@ struct WalkDev {
                                      // k-chunks c with c % shard_count == shard_rank (count <= 1: all of them)
   uint32_t *bits, *bits_local, *bits_best;  // logical word 0 (guards before and after)
   uint32_t *bits_fbest;                     // lowest-F pivot (when track_fbest)
+  // partner windows of the pivot for every position p (neighbourhood kernel): bit t of
+  // win_f[p] is the bit of s_{p+t}, bit t of win_r[p] that of s_{p-t} (0 outside 0..L-1);
+  // indices -kWinGuard .. L-1+kWinGuard
+  uint32_t *win_f, *win_r;
   int32_t *C, *C_local;
   float4 *T;          // per k: (Tp4, Tm4, Tp2, Tm2), scaled by 2^(-alpha*e)
   float *score;       // FP32 filter score of window position i at [i-1]
@@ -136,8 +141,11 @@ cudaError_t launch_hot_plain(WalkDev *hdr_one, uint32_t N, cudaStream_t s);
 cudaError_t launch_select(const LaunchCtx &c);
 cudaError_t launch_recheck(const LaunchCtx &c);
 cudaError_t launch_decide(const LaunchCtx &c);
+cudaError_t launch_step_tail(const LaunchCtx &c);  // select..apply in one kernel, short walks only
+constexpr uint32_t kTailMaxL = kApplyChunk;      // walks up to this length (one update chunk, one re-check chunk)
+constexpr uint32_t kTailMaxN = 2048;             // and windows up to this size (one warp selects)
 cudaError_t launch_start_init(const LaunchCtx &c);
-size_t hot_batched_smem(uint32_t tile_sb);
+size_t hot_batched_smem(uint32_t tile_sb, bool masked);  // masked: the short-walk variants (five tables per group)
 bool hot_config_supported(uint32_t threads, uint32_t tile_sb);  // block sizes 128/256/512, tiles 16/32
 uint32_t hot_flush_for(uint32_t maxL);  // super-blocks per block sum for a batch whose longest walk is maxL
 

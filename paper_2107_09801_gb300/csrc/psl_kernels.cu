@@ -125,112 +125,25 @@ __global__ void k_start_init(WalkDev *hdr, const uint32_t *active, uint32_t nact
 // apply: the O(L) update pass (init / move / switch) fused with the next window's
 // tables, PSL, sum of |T| and the near-peak list; the last block to arrive finalises.
 // ------------------------------------------------------------------------------------
-__device__ __forceinline__ void apply_one(WalkDev &W, uint32_t chunk) {
+// Block reductions of one (walk, chunk) pair of the update pass, the chunk's partial record,
+// and -- in the last block of the walk to arrive -- the walk's finalisation: the new pivot's
+// bits and partner windows, PSL, sum of |T|, exact F (NEED_F: init and switch), the lowest-F
+// pivot, best-PSL and local-best bookkeeping, the next window's start.
+template <bool NEED_F>
+__device__ __forceinline__ void apply_finish(WalkDev &W, uint32_t chunk, uint32_t mode, bool keep_local, int kstar,
+                                             int nflip, uint32_t alpha, int pmax, float sabs,
+                                             uint32_t (&F)[kWideLimbs]) {
   __shared__ int s_max[8];
   __shared__ float s_sum[8];
-  __shared__ uint32_t s_F[256 / 32][kWideLimbs];
+  __shared__ uint32_t s_F[NEED_F ? 256 / 32 : 1][kWideLimbs];
   __shared__ uint32_t s_last, s_fcopy;
-  if (W.status != kRunning) return;
-  if (chunk >= W.nchunk_apply) return;
+  constexpr bool need_F = NEED_F;
   const int L = (int)W.L;
-  const int k0 = (int)chunk * kApplyChunk, k1 = min(k0 + kApplyChunk, L);
-  const uint32_t mode = W.mode;
-  const uint32_t alpha = W.alpha_next;
-  const float inv2e = ldexpf(1.f, -W.e);
-  const int thr = W.ktau_thr;
-  const bool keep_local = (mode == kModeInit) || W.improved;
-  const bool need_F = mode != kModeMove;
-  const int kstar = (int)W.kstar;
-  const int sk = (mode == kModeMove) ? sval(W.bits, kstar) : 0;
-  const int nflip = (int)W.nflip;
-
-  int pmax = 0;
-  float sabs = 0.f;
-  uint32_t F[kWideLimbs];
-  wide_zero(F);
-  // the ordinary step (one move): a lean loop, unrolled so that the loads of several k
-  // are in flight together
-  const int kfirst = k0 + (int)threadIdx.x;
-  int kmove = (mode == kModeMove) ? max(kfirst, 1) : k1;
-  if (mode == kModeMove && kfirst == 0) {
-    W.C[0] = L;
-    if (keep_local) W.C_local[0] = L;
-    kmove = kfirst + (int)blockDim.x;
-  }
-  const int *__restrict__ Cin = W.C;
-  const uint32_t *__restrict__ bits_now = W.bits;
-#pragma unroll 4
-  for (int k = kmove; k < k1; k += blockDim.x) {
-    // Sec. 3: C'_k = C_k - 2 s_j (s_{j+k} + s_{j-k}), absent partners count 0
-    int part = 0;
-    if (kstar + k < L) part += sval(bits_now, kstar + k);
-    if (kstar >= k) part += sval(bits_now, kstar - k);
-    const int c = Cin[k] - 2 * sk * part;
-    W.C[k] = c;
-    if (keep_local) W.C_local[k] = c;
-    const int a = c < 0 ? -c : c;
-    pmax = max(pmax, a);
-    const float4 t = tables_for(c, alpha, inv2e);
-    W.T[k] = t;
-    sabs += absmax4(t);
-    if (a >= thr) {
-      const uint32_t at = atomicAdd(&W.nktau, 1u);
-      W.ktau[at] = make_int2(k, c);
-    }
-  }
-  for (int k = (mode == kModeMove) ? k1 : kfirst; k < k1; k += blockDim.x) {
-    int c;
-    if (k == 0) {
-      c = L;
-    } else if (mode == kModeInit) {
-      c = W.C[k];
-    } else if (mode == kModeMove) {
-      // Sec. 3: C'_k = C_k - 2 s_j (s_{j+k} + s_{j-k}), absent partners count 0
-      int part = 0;
-      if (kstar + k < L) part += sval(W.bits, kstar + k);
-      if (kstar >= k) part += sval(W.bits, kstar - k);
-      c = W.C[k] - 2 * sk * part;
-    } else {
-      // several flips of local_best at once: a product s_i s_{i+k} changes sign exactly
-      // when one of its two positions is flipped
-      c = W.C_local[k];
-      for (int q = 0; q < nflip; q++) {
-        const int f = (int)W.flips[q];
-        const int sf = sval(W.bits_local, f);
-        const int p = f + k, m = f - k;
-        if (p < L) {
-          bool in = false;
-          for (int r = 0; r < nflip; r++) in |= ((int)W.flips[r] == p);
-          if (!in) c -= 2 * sf * sval(W.bits_local, p);
-        }
-        if (m >= 0) {
-          bool in = false;
-          for (int r = 0; r < nflip; r++) in |= ((int)W.flips[r] == m);
-          if (!in) c -= 2 * sf * sval(W.bits_local, m);
-        }
-      }
-    }
-    W.C[k] = c;
-    if (keep_local) W.C_local[k] = c;
-    if (k >= 1) {
-      const int a = c < 0 ? -c : c;
-      pmax = max(pmax, a);
-      const float4 t = tables_for(c, alpha, inv2e);
-      W.T[k] = t;
-      sabs += absmax4(t);
-      if (a >= thr) {
-        const uint32_t at = atomicAdd(&W.nktau, 1u);
-        W.ktau[at] = make_int2(k, c);
-      }
-      if (need_F) add_pow_rt(F, (uint32_t)a, alpha);
-    }
-  }
-  // block reductions
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   pmax = warp_max(pmax);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) sabs += __shfl_xor_sync(0xffffffffu, sabs, o);
-  if (need_F) {
+  if constexpr (NEED_F) {
     for (int o = 16; o > 0; o >>= 1) {
       uint32_t other[kWideLimbs];
 #pragma unroll
@@ -241,7 +154,7 @@ __device__ __forceinline__ void apply_one(WalkDev &W, uint32_t chunk) {
   if (lane == 0) {
     s_max[warp] = pmax;
     s_sum[warp] = sabs;
-    if (need_F) wide_store(s_F[warp], F);
+    if constexpr (NEED_F) wide_store(s_F[warp], F);
   }
   __syncthreads();
   uint32_t *part = W.ap_part + (size_t)chunk * kApplyPartStride;
@@ -253,7 +166,7 @@ __device__ __forceinline__ void apply_one(WalkDev &W, uint32_t chunk) {
     for (int w = 0; w < (int)(blockDim.x >> 5); w++) {
       m = max(m, s_max[w]);
       s += s_sum[w];
-      if (need_F) {
+      if constexpr (NEED_F) {
         uint32_t t[kWideLimbs];
         wide_load(t, s_F[w]);
         wide_add(Fb, t);
@@ -283,6 +196,20 @@ __device__ __forceinline__ void apply_one(WalkDev &W, uint32_t chunk) {
     if (threadIdx.x == 0) W.bits[kstar >> 5] ^= 1u << (kstar & 31);
   }
   __syncthreads();
+  // partner windows of the new pivot: one move changes 32 entries of each, any other pivot
+  // (the start, a perturbed local_best) is rebuilt whole
+  if (mode == kModeMove) {
+    const int t = (int)threadIdx.x;
+    if (t < 32)
+      W.win_f[kstar - t] ^= 1u << t;  // s_{p+t} with p + t = k*
+    else if (t < 64)
+      W.win_r[kstar + (t - 32)] ^= 1u << (t - 32);  // s_{p-t} with p - t = k*
+  } else {
+    for (int p = (int)threadIdx.x - kWinGuard; p < L + kWinGuard; p += blockDim.x) {
+      W.win_f[p] = window32(W.bits, p);
+      W.win_r[p] = __brev(window32(W.bits, p - 31));
+    }
+  }
   if (keep_local)
     for (int w = threadIdx.x; w < nw; w += blockDim.x) W.bits_local[w] = W.bits[w];
   if (mode == kModeInit)
@@ -339,6 +266,170 @@ __device__ __forceinline__ void apply_one(WalkDev &W, uint32_t chunk) {
     __syncthreads();
     if (s_fcopy)
       for (int w = threadIdx.x; w < nw; w += blockDim.x) W.bits_fbest[w] = W.bits[w];
+  }
+}
+
+
+__device__ __forceinline__ void apply_one(WalkDev &W, uint32_t chunk) {
+  if (W.status != kRunning) return;
+  if (chunk >= W.nchunk_apply) return;
+  const uint32_t mode = W.mode;
+  if (mode == kModeMove) return;  // k_apply_move's work
+  const int L = (int)W.L;
+  const int k0 = (int)chunk * kApplyChunk, k1 = min(k0 + kApplyChunk, L);
+  const uint32_t alpha = W.alpha_next;
+  const float inv2e = ldexpf(1.f, -W.e);
+  const int thr = W.ktau_thr;
+  const bool keep_local = (mode == kModeInit) || W.improved;
+  const int nflip = (int)W.nflip;
+
+  int pmax = 0;
+  float sabs = 0.f;
+  uint32_t F[kWideLimbs];
+  wide_zero(F);
+  for (int k = k0 + (int)threadIdx.x; k < k1; k += blockDim.x) {
+    int c;
+    if (k == 0) {
+      c = L;
+    } else if (mode == kModeInit) {
+      c = W.C[k];
+    } else {
+      // several flips of local_best at once: a product s_i s_{i+k} changes sign exactly
+      // when one of its two positions is flipped
+      c = W.C_local[k];
+      for (int q = 0; q < nflip; q++) {
+        const int f = (int)W.flips[q];
+        const int sf = sval(W.bits_local, f);
+        const int p = f + k, m = f - k;
+        if (p < L) {
+          bool in = false;
+          for (int r = 0; r < nflip; r++) in |= ((int)W.flips[r] == p);
+          if (!in) c -= 2 * sf * sval(W.bits_local, p);
+        }
+        if (m >= 0) {
+          bool in = false;
+          for (int r = 0; r < nflip; r++) in |= ((int)W.flips[r] == m);
+          if (!in) c -= 2 * sf * sval(W.bits_local, m);
+        }
+      }
+    }
+    W.C[k] = c;
+    if (keep_local) W.C_local[k] = c;
+    if (k >= 1) {
+      const int a = c < 0 ? -c : c;
+      pmax = max(pmax, a);
+      const float4 t = tables_for(c, alpha, inv2e);
+      W.T[k] = t;
+      sabs += absmax4(t);
+      if (a >= thr) {
+        const uint32_t at = atomicAdd(&W.nktau, 1u);
+        W.ktau[at] = make_int2(k, c);
+      }
+      add_pow_rt(F, (uint32_t)a, alpha);
+    }
+  }
+  apply_finish<true>(W, chunk, mode, keep_local, 0, nflip, alpha, pmax, sabs, F);
+}
+
+// The update pass of an ordinary step (one move, Sec. 3: C'_k = C_k - 2 s_j (s_{j+k} +
+// s_{j-k}), absent partners count 0) with the next window's tables for exponent A: four
+// consecutive shifts per thread and iteration, C read and written as int4, the mover's
+// partner bits for those shifts from one entry of each partner window, the table powers
+// unrolled for A.
+template <int A>
+__device__ __forceinline__ void apply_move_one(WalkDev &W, uint32_t chunk) {
+  const int L = (int)W.L;
+  const int k0 = (int)chunk * kApplyChunk, k1 = min(k0 + kApplyChunk, L);
+  const float inv2e = ldexpf(1.f, -W.e);
+  const int thr = W.ktau_thr;
+  const bool keep_local = W.improved != 0;
+  const int kstar = (int)W.kstar;
+  const int sk = sval(W.bits, kstar);
+  const int kplus = L - 1 - kstar;  // shifts k <= kplus have the partner k* + k, k <= k* the partner k* - k
+  int *__restrict__ C = W.C;
+  int *__restrict__ Cl = W.C_local;
+  float4 *__restrict__ T = W.T;
+  int pmax = 0;
+  float sabs = 0.f;
+  for (int kq = k0 + 4 * (int)threadIdx.x; kq < k1; kq += 4 * (int)blockDim.x) {
+    int c[4];
+    if (kq + 3 < L) {
+      const int4 v = *reinterpret_cast<const int4 *>(C + kq);
+      c[0] = v.x, c[1] = v.y, c[2] = v.z, c[3] = v.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; q++) c[q] = kq + q < L ? C[kq + q] : 0;
+    }
+    // bit q: s_{k*+kq+q} and s_{k*-kq-q} (past either end the bits read 0; those shifts have no partner)
+    const uint32_t up = W.win_f[min(kstar + kq, L)], dn = W.win_r[max(kstar - kq, -1)];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int k = kq + q;
+      const int part = (k <= kplus ? 1 - 2 * (int)((up >> q) & 1u) : 0) + (k <= kstar ? 1 - 2 * (int)((dn >> q) & 1u) : 0);
+      c[q] = (k == 0) ? L : c[q] - 2 * sk * part;
+    }
+    if (kq + 3 < L) {
+      *reinterpret_cast<int4 *>(C + kq) = make_int4(c[0], c[1], c[2], c[3]);
+      if (keep_local) *reinterpret_cast<int4 *>(Cl + kq) = make_int4(c[0], c[1], c[2], c[3]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; q++)
+        if (kq + q < L) {
+          C[kq + q] = c[q];
+          if (keep_local) Cl[kq + q] = c[q];
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int k = kq + q;
+      if (k >= 1 && k < L) {
+        const int a = c[q] < 0 ? -c[q] : c[q];
+        const float4 tv = tables_for(c[q], (uint32_t)A, inv2e);
+        T[k] = tv;
+        pmax = max(pmax, a);
+        sabs += absmax4(tv);
+        if (a >= thr) {
+          const uint32_t at = atomicAdd(&W.nktau, 1u);
+          W.ktau[at] = make_int2(k, c[q]);
+        }
+      }
+    }
+  }
+  uint32_t F[kWideLimbs];  // unused: an ordinary move takes F from the exact re-check
+  apply_finish<false>(W, chunk, kModeMove, keep_local, kstar, 0, (uint32_t)A, pmax, sabs, F);
+}
+
+__device__ __forceinline__ void apply_move_dispatch(WalkDev &W, uint32_t chunk) {
+  switch (W.alpha_next) {
+    case 1: apply_move_one<1>(W, chunk); break;
+    case 2: apply_move_one<2>(W, chunk); break;
+    case 3: apply_move_one<3>(W, chunk); break;
+    case 4: apply_move_one<4>(W, chunk); break;
+    case 5: apply_move_one<5>(W, chunk); break;
+    case 6: apply_move_one<6>(W, chunk); break;
+    case 7: apply_move_one<7>(W, chunk); break;
+    case 8: apply_move_one<8>(W, chunk); break;
+    case 9: apply_move_one<9>(W, chunk); break;
+    case 10: apply_move_one<10>(W, chunk); break;
+    case 11: apply_move_one<11>(W, chunk); break;
+    case 12: apply_move_one<12>(W, chunk); break;
+    case 13: apply_move_one<13>(W, chunk); break;
+    case 14: apply_move_one<14>(W, chunk); break;
+    case 15: apply_move_one<15>(W, chunk); break;
+    default: apply_move_one<16>(W, chunk); break;
+  }
+}
+
+// persistent grid over (walk, chunk) pairs of the schedule: the walks whose step was an
+// ordinary move (every other walk is the work of k_apply)
+__global__ void __launch_bounds__(256) k_apply_move(WalkDev *hdr, const uint32_t *active, const Schedule *sched) {
+  const uint32_t nch = sched->max_chunk_apply, V = sched->nactive * nch;
+  for (uint32_t v = blockIdx.x; v < V; v += gridDim.x) {
+    WalkDev &W = hdr[active[v / nch]];
+    const uint32_t chunk = v % nch;
+    if (W.status != kRunning || chunk >= W.nchunk_apply || W.mode != kModeMove) continue;  // uniform over the block
+    __syncthreads();  // shared reduction buffers of the previous pair are free
+    apply_move_dispatch(W, chunk);
   }
 }
 
@@ -500,6 +591,8 @@ __device__ __forceinline__ void select_one(WalkDev &W) {
 // compaction goes 32 positions at a time (ballot + popcount keeps scan order) and every
 // reduction is a shuffle, so many short walks are served at once without block barriers.
 constexpr int kSelectWarpN = 2048;
+static_assert(kTailMaxN == (uint32_t)kSelectWarpN && kTailMaxL <= (uint32_t)kRecheckChunk,
+              "the fused step tail needs one warp selection, one update chunk and one re-check chunk per walk");
 
 __device__ __forceinline__ void select_warp(WalkDev &W) {
   const int lane = threadIdx.x & 31;
@@ -609,9 +702,43 @@ __global__ void __launch_bounds__(1024) k_select(WalkDev *hdr, const uint32_t *a
 // candidates, one CTA per (chunk of k, candidate); positive and negative parts are
 // accumulated separately as unsigned 384-bit integers.
 // ------------------------------------------------------------------------------------
+template <int A, int NL>
+__device__ void recheck_body_n(const WalkDev &W, int j, int kbeg, int kend, uint32_t (&pos)[kWideLimbs],
+                               uint32_t (&neg)[kWideLimbs]) {
+  const int L = (int)W.L;
+  const int sj = sval(W.bits, j);
+  uint32_t P[NL], Q[NL];
+#pragma unroll
+  for (int i = 0; i < NL; i++) P[i] = Q[i] = 0;
+  for (int k = kbeg + (int)threadIdx.x; k < kend; k += blockDim.x) {
+    int part = 0;
+    if (j + k < L) part += sval(W.bits, j + k);
+    if (j >= k) part += sval(W.bits, j - k);
+    if (part == 0) continue;
+    const int c = W.C[k];
+    const int cn = c - 2 * sj * part;
+    add_pow_n<A, NL>(P, (uint32_t)(cn < 0 ? -cn : cn));
+    add_pow_n<A, NL>(Q, (uint32_t)(c < 0 ? -c : c));
+  }
+#pragma unroll
+  for (int i = 0; i < kWideLimbs; i++) pos[i] = i < NL ? P[i] : 0u, neg[i] = i < NL ? Q[i] : 0u;
+}
+
 template <int A>
 __device__ void recheck_body(const WalkDev &W, int j, int kbeg, int kend, uint32_t (&pos)[kWideLimbs],
                              uint32_t (&neg)[kWideLimbs]) {
+  // every |C_k + delta| of this window is below 2^e, so each power has at most A e bits and
+  // a thread's sum of fewer than 2^20 of them at most A e + 20: narrower accumulators
+  // where that fits
+  const int bits = A * (int)W.e + 20;
+  if (bits <= 128) {
+    recheck_body_n<A, 4>(W, j, kbeg, kend, pos, neg);
+    return;
+  }
+  if (bits <= 256) {
+    recheck_body_n<A, 8>(W, j, kbeg, kend, pos, neg);
+    return;
+  }
   const int L = (int)W.L;
   const int sj = sval(W.bits, j);
   for (int k = kbeg + (int)threadIdx.x; k < kend; k += blockDim.x) {
@@ -880,10 +1007,41 @@ __global__ void __launch_bounds__(256) k_decide(WalkDev *hdr, const uint32_t *ac
 }
 
 // ------------------------------------------------------------------------------------
+// the step after the neighbourhood score for batches of short walks (every walk with one
+// update chunk, one re-check chunk and a window selected by one warp): one block per walk
+// runs selection, exact re-check, decision and update back to back, instead of four
+// launches of latency-bound kernels
+// ------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(256, 3) k_step_tail(WalkDev *hdr, const uint32_t *active, Schedule *sched) {
+  // the neighbourhood kernel of this step has finished: rearm its work counter
+  if (blockIdx.x == 0 && threadIdx.x == 0) sched->hot_next = 0;
+  for (uint32_t a = blockIdx.x; a < sched->nactive; a += gridDim.x) {
+    WalkDev &W = hdr[active[a]];
+    __syncthreads();  // the previous walk's shared buffers are free
+    if (W.status != kRunning) continue;  // one reading for the block: nothing below changes it before it is read
+    if (threadIdx.x < 32) select_warp(W);
+    __syncthreads();  // candidates, bound and window PSL are visible to the block
+    const uint32_t nslots = min(W.ncand, (uint32_t)kQcap);
+    for (uint32_t qslot = 0; qslot < nslots; qslot++) {
+      __syncthreads();
+      recheck_one(W, 0, qslot);
+    }
+    __syncthreads();  // re-check partials are visible
+    decide_one(W);
+    __syncthreads();  // the decision (mode, k*, flips, next exponent) is visible
+    if (W.mode == kModeMove)
+      apply_move_dispatch(W, 0);
+    else
+      apply_one(W, 0);
+  }
+}
+
+// ------------------------------------------------------------------------------------
 // launchers
 // ------------------------------------------------------------------------------------
 // resident blocks per SM of the other persistent kernels (one wave each)
-static uint32_t g_apply_per_sm = 4, g_select_per_sm = 1, g_recheck_per_sm = 3, g_decide_per_sm = 4;
+static uint32_t g_apply_per_sm = 4, g_apply_move_per_sm = 4, g_select_per_sm = 1, g_recheck_per_sm = 3,
+                g_decide_per_sm = 4, g_tail_per_sm = 4;
 
 cudaError_t launch_init_bits(const LaunchCtx &c) {
   const uint32_t maxw = (c.maxL + 31) / 32 + 2 * kGuardWords;
@@ -904,6 +1062,10 @@ cudaError_t launch_start_init(const LaunchCtx &c) {
 }
 
 cudaError_t launch_apply(const LaunchCtx &c) {
+  // walks whose step was an ordinary move, then the rest (initialisation, phase switch)
+  k_apply_move<<<g_apply_move_per_sm * c.sm_count, 256, 0, c.stream>>>(c.hdr, c.active, c.sched);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
   k_apply<<<g_apply_per_sm * c.sm_count, 256, 0, c.stream>>>(c.hdr, c.active, c.sched);
   return cudaGetLastError();
 }
@@ -917,6 +1079,8 @@ static cudaError_t blocks_per_sm(const void *f, int threads, uint32_t *out) {
 
 static cudaError_t prepare_kernels_once() {
   cudaError_t e0 = blocks_per_sm((const void *)k_apply, 256, &g_apply_per_sm);
+  if (e0 == cudaSuccess) e0 = blocks_per_sm((const void *)k_apply_move, 256, &g_apply_move_per_sm);
+  if (e0 == cudaSuccess) e0 = blocks_per_sm((const void *)k_step_tail, 256, &g_tail_per_sm);
   if (e0 == cudaSuccess) e0 = blocks_per_sm((const void *)k_select, 1024, &g_select_per_sm);
   if (e0 == cudaSuccess) e0 = blocks_per_sm((const void *)k_recheck, 256, &g_recheck_per_sm);
   if (e0 == cudaSuccess) e0 = blocks_per_sm((const void *)k_decide, 256, &g_decide_per_sm);
@@ -942,6 +1106,11 @@ cudaError_t launch_select(const LaunchCtx &c) {
 
 cudaError_t launch_recheck(const LaunchCtx &c) {
   k_recheck<<<g_recheck_per_sm * c.sm_count, 256, 0, c.stream>>>(c.hdr, c.active, c.sched);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_step_tail(const LaunchCtx &c) {
+  k_step_tail<<<g_tail_per_sm * c.sm_count, 256, 0, c.stream>>>(c.hdr, c.active, c.sched);
   return cudaGetLastError();
 }
 

@@ -23,8 +23,9 @@ namespace {
 
 thread_local std::string g_init_error;
 
-enum ProfKind { kPHot = 0, kPSelect, kPRecheck, kPDecide, kPApply, kPHotPlain, kPInit, kPGraph, kProfKinds };
-const char *kProfNames[kProfKinds] = {"hot", "select", "recheck", "decide", "apply", "hot_plain", "init", "graph"};
+enum ProfKind { kPHot = 0, kPSelect, kPRecheck, kPDecide, kPApply, kPHotPlain, kPInit, kPGraph, kPTail, kProfKinds };
+const char *kProfNames[kProfKinds] = {"hot", "select", "recheck", "decide", "apply", "hot_plain", "init", "graph",
+                                      "tail"};
 
 double now_s() {
   using namespace std::chrono;
@@ -34,7 +35,8 @@ double now_s() {
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 struct Layout {
-  size_t bits, bits_local, bits_best, bits_fbest, C, C_local, T, score, score_part, pslj, ktau, cand, rc_part, ap_part, trace, total;
+  size_t bits, bits_local, bits_best, bits_fbest, win_f, win_r, C, C_local, T, score, score_part, pslj, ktau, cand,
+      rc_part, ap_part, trace, total;
 };
 
 Layout layout_for(uint32_t L, uint32_t N, uint32_t trace_cap) {
@@ -53,6 +55,8 @@ Layout layout_for(uint32_t L, uint32_t N, uint32_t trace_cap) {
   o.bits_local = take(words * 4);
   o.bits_best = take(words * 4);
   o.bits_fbest = take(words * 4);
+  o.win_f = take(((size_t)L + 2 * kWinGuard) * 4);
+  o.win_r = take(((size_t)L + 2 * kWinGuard) * 4);
   o.C = take((size_t)L * 4);
   o.C_local = take((size_t)L * 4);
   o.T = take((size_t)L * 16);
@@ -145,6 +149,7 @@ struct psl_ctx {
   uint32_t nitems = 0, max_chunk_apply = 1, max_chunk_rc = 1;
   int64_t next_id = 0;
   uint32_t hot_flush_sb = 8;  // super-blocks per block sum of the neighbourhood kernel
+  bool tail_fused = false;    // every running walk is short: select..apply run as one kernel
   uint32_t sm_count = 152;   // SMs the persistent kernels are sized for
   uint32_t dev_sms = 152;    // SMs of the device
   std::string err;
@@ -537,6 +542,8 @@ static void fill_header(psl_ctx *ctx, HostWalk &w, WalkDev &h) {
   h.bits_best = (uint32_t *)(base + w.lay.bits_best) + kGuardWords;
   h.bits_fbest = (uint32_t *)(base + w.lay.bits_fbest) + kGuardWords;
   h.track_fbest = p.alpha1 == p.alpha2 ? 1u : 0u;
+  h.win_f = (uint32_t *)(base + w.lay.win_f) + kWinGuard;
+  h.win_r = (uint32_t *)(base + w.lay.win_r) + kWinGuard;
   h.C = (int32_t *)(base + w.lay.C);
   h.C_local = (int32_t *)(base + w.lay.C_local);
   h.T = (float4 *)(base + w.lay.T);
@@ -576,6 +583,14 @@ static int rebuild_active(psl_ctx *ctx) {
   if (fb != ctx->hot_flush_sb) {
     ctx->hot_flush_sb = fb;
     drop_graph(ctx);  // captured with the other kernel variant
+  }
+  bool short_only = !ctx->active.empty();
+  for (uint32_t s : ctx->active)
+    short_only = short_only && ctx->h_hdr[s].L <= kTailMaxL && ctx->h_hdr[s].N <= kTailMaxN &&
+                 ctx->h_hdr[s].shard_count <= 1;
+  if (short_only != ctx->tail_fused) {
+    ctx->tail_fused = short_only;
+    drop_graph(ctx);  // captured with the other kernel sequence
   }
   // Split every walk's k range into chunks when the neighbour blocks alone would leave
   // SMs idle (few walks, or a long walk on its own): aim for about four blocks per SM.
@@ -747,8 +762,14 @@ static int refresh_headers(psl_ctx *ctx) {
 static cudaError_t enqueue_batched_step(psl_ctx *ctx, const LaunchCtx &c, bool captured) {
   cudaError_t (*fns[5])(const LaunchCtx &) = {launch_hot_batched, launch_select, launch_recheck, launch_decide,
                                                launch_apply};
-  const int kinds[5] = {kPHot, kPSelect, kPRecheck, kPDecide, kPApply};
-  for (int q = 0; q < 5; q++) {
+  int kinds[5] = {kPHot, kPSelect, kPRecheck, kPDecide, kPApply};
+  int n = 5;
+  if (ctx->tail_fused) {  // short walks only: selection, re-check, decision and update in one kernel
+    fns[1] = launch_step_tail;
+    kinds[1] = kPTail;
+    n = 2;
+  }
+  for (int q = 0; q < n; q++) {
     cudaError_t e = captured ? gprof_begin(ctx, kinds[q]) : prof_begin(ctx, kinds[q]);
     if (e == cudaSuccess) e = fns[q](c);
     if (e == cudaSuccess) e = captured ? gprof_end(ctx, kinds[q]) : prof_end(ctx, kinds[q]);
@@ -763,7 +784,7 @@ static int capture_graph(psl_ctx *ctx) {
   drop_graph(ctx);
   const uint32_t G = (uint32_t)ctx->cfg.steps_per_graph;
   LaunchCtx c = launch_ctx(ctx, ctx->d_active, ctx->d_sched);
-  if (ctx->prof) CK(gprof_reserve(ctx, (size_t)G * 5));
+  if (ctx->prof) CK(gprof_reserve(ctx, (size_t)G * 5));  // at most five kernels a step
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;

@@ -145,6 +145,35 @@ def test_batch_composition_invariance(P):
         assert np.array_equal(st["C"], st1["C"]) and np.array_equal(st["pivot"], st1["pivot"])
 
 
+def test_fused_step_tail_matches_separate_kernels(P):
+    """Short walks alone run selection, re-check, decision and update as one kernel; with one
+    long walk in the batch they run as four.  Both follow the oracle step by step."""
+    specs = [W.WalkSpec(L=L, seed=60 + r, alpha1=1 + r % 5, alpha2=6 + r % 8, budget=40, n_lmt=nl, ls_lmt=3,
+                        flip_lmt=4, topk=1 + r % 3)
+             for r, (L, nl) in enumerate([(255, 255), (1023, 1023), (2047, 700), (8192, 2048), (31, 31), (700, 6912)])]
+    long = W.WalkSpec(L=10000, seed=9, budget=40, ls_lmt=3)
+    with P.Context(arena_bytes=ARENA, max_walks=16, steps_per_graph=8) as ctx:
+        ids = [submit_spec(ctx, s) for s in specs]
+        ctx.profile(1)
+        ctx.run()
+        assert ctx.profile_read()["tail"][0] > 0
+        fused = [(ctx.trace(i, s.budget), ctx.export_state(i)) for i, s in zip(ids, specs)]
+    with P.Context(arena_bytes=ARENA, max_walks=16, steps_per_graph=8) as ctx:
+        ids = [submit_spec(ctx, s) for s in specs + [long]]
+        ctx.profile(1)
+        ctx.run()
+        assert ctx.profile_read()["tail"][0] == 0
+        sep = [(ctx.trace(i, s.budget), ctx.export_state(i)) for i, s in zip(ids, specs + [long])]
+    for s, (tf, sf), (ts, ss) in zip(specs, fused, sep):
+        w = oracle_walk(s)
+        compare_traces(tf, w.run(s.budget), f"fused L={s.L}")
+        compare_final_state(sf, w)
+        assert same_decisions(tf, ts)
+        assert np.array_equal(sf["C"], ss["C"])
+    w = oracle_walk(long)
+    compare_traces(sep[-1][0], w.run(long.budget), "long")
+
+
 def test_resizing_sm_share_mid_run_keeps_results(P):
     """The SM count a context's kernels are sized for changes which blocks score which k
     range, never a decision: resize between steps and compare with the oracle."""
@@ -541,7 +570,12 @@ def test_graph_profile_and_transfer_counts(P):
         ctx.profile(1)                   # every kernel: the graph is captured again
         ctx.step(4)
         pr = ctx.profile_read()
-        assert all(pr[k][0] == 4 for k in ("hot", "select", "recheck", "decide", "apply")), pr
+        tail = ("select", "recheck", "decide", "apply")
+        assert pr["hot"][0] == 4, pr
+        if pr["tail"][0]:                # short walks only: the step after the score is one kernel
+            assert pr["tail"][0] == 4 and all(pr[k][0] == 0 for k in tail), pr
+        else:
+            assert all(pr[k][0] == 4 for k in tail), pr
         ctx.profile(0)
         ctx.set_steps_per_graph(0)
         ctx.run()
