@@ -702,24 +702,51 @@ __global__ void __launch_bounds__(1024) k_select(WalkDev *hdr, const uint32_t *a
 // candidates, one CTA per (chunk of k, candidate); positive and negative parts are
 // accumulated separately as unsigned 384-bit integers.
 // ------------------------------------------------------------------------------------
+// Delta F of neighbour j over shifts kbeg..kend-1, accumulated as two unsigned sums
+// (|C_k + delta|^A and |C_k|^A over the shifts with delta != 0) in NL-limb registers: four
+// consecutive shifts per thread and iteration, C read as int4, the neighbour's partner bits
+// for those shifts from one entry of each partner window.
+template <int A, int NL, typename Acc>
+__device__ __forceinline__ void recheck_quads(const WalkDev &W, int j, int kbeg, int kend, Acc &P, Acc &Q) {
+  const int L = (int)W.L;
+  const int sj = sval(W.bits, j);
+  const int kplus = L - 1 - j;  // shifts k <= kplus have the partner j + k, k <= j the partner j - k
+  const int *__restrict__ C = W.C;
+  for (int kq = (kbeg & ~3) + 4 * (int)threadIdx.x; kq < kend; kq += 4 * (int)blockDim.x) {
+    int c[4];
+    if (kq + 3 < L) {
+      const int4 v = *reinterpret_cast<const int4 *>(C + kq);
+      c[0] = v.x, c[1] = v.y, c[2] = v.z, c[3] = v.w;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; q++) c[q] = kq + q < L ? C[kq + q] : 0;
+    }
+    // bit q: s_{j+kq+q} and s_{j-kq-q} (past either end the bits read 0; those shifts have no partner)
+    const uint32_t up = W.win_f[min(j + kq, L)], dn = W.win_r[max(j - kq, -1)];
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+      const int k = kq + q;
+      const int part = (k <= kplus ? 1 - 2 * (int)((up >> q) & 1u) : 0) + (k <= j ? 1 - 2 * (int)((dn >> q) & 1u) : 0);
+      if (k < kbeg || k >= kend || part == 0) continue;
+      const int cn = c[q] - 2 * sj * part;
+      if constexpr (NL == kWideLimbs) {
+        add_pow<A>(P, (uint32_t)(cn < 0 ? -cn : cn));
+        add_pow<A>(Q, (uint32_t)(c[q] < 0 ? -c[q] : c[q]));
+      } else {
+        add_pow_n<A, NL>(P, (uint32_t)(cn < 0 ? -cn : cn));
+        add_pow_n<A, NL>(Q, (uint32_t)(c[q] < 0 ? -c[q] : c[q]));
+      }
+    }
+  }
+}
+
 template <int A, int NL>
 __device__ void recheck_body_n(const WalkDev &W, int j, int kbeg, int kend, uint32_t (&pos)[kWideLimbs],
                                uint32_t (&neg)[kWideLimbs]) {
-  const int L = (int)W.L;
-  const int sj = sval(W.bits, j);
   uint32_t P[NL], Q[NL];
 #pragma unroll
   for (int i = 0; i < NL; i++) P[i] = Q[i] = 0;
-  for (int k = kbeg + (int)threadIdx.x; k < kend; k += blockDim.x) {
-    int part = 0;
-    if (j + k < L) part += sval(W.bits, j + k);
-    if (j >= k) part += sval(W.bits, j - k);
-    if (part == 0) continue;
-    const int c = W.C[k];
-    const int cn = c - 2 * sj * part;
-    add_pow_n<A, NL>(P, (uint32_t)(cn < 0 ? -cn : cn));
-    add_pow_n<A, NL>(Q, (uint32_t)(c < 0 ? -c : c));
-  }
+  recheck_quads<A, NL>(W, j, kbeg, kend, P, Q);
 #pragma unroll
   for (int i = 0; i < kWideLimbs; i++) pos[i] = i < NL ? P[i] : 0u, neg[i] = i < NL ? Q[i] : 0u;
 }
@@ -739,18 +766,7 @@ __device__ void recheck_body(const WalkDev &W, int j, int kbeg, int kend, uint32
     recheck_body_n<A, 8>(W, j, kbeg, kend, pos, neg);
     return;
   }
-  const int L = (int)W.L;
-  const int sj = sval(W.bits, j);
-  for (int k = kbeg + (int)threadIdx.x; k < kend; k += blockDim.x) {
-    int part = 0;
-    if (j + k < L) part += sval(W.bits, j + k);
-    if (j >= k) part += sval(W.bits, j - k);
-    if (part == 0) continue;
-    const int c = W.C[k];
-    const int cn = c - 2 * sj * part;
-    add_pow<A>(pos, (uint32_t)(cn < 0 ? -cn : cn));
-    add_pow<A>(neg, (uint32_t)(c < 0 ? -c : c));
-  }
+  recheck_quads<A, kWideLimbs>(W, j, kbeg, kend, pos, neg);
 }
 
 __device__ __forceinline__ void recheck_one(WalkDev &W, uint32_t chunk, uint32_t qslot) {
