@@ -83,3 +83,48 @@ def test_shard_argument_errors(P):
             ctx.shard_layout(wid)                 # not a sharded walk
         with pytest.raises(P.PslError):
             ctx.submit_ex(65535, 1, 4, 13, 5, shard_rank=0, shard_count=2)   # needs a context of its own
+
+
+def _shard_rank(rank, world, port, q, spec_kw):
+    import os
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import paper_2107_09801_gb300 as P
+    from paper_2107_09801_gb300.sharded import ShardedWalk, torch_exchange
+    L, budget = spec_kw["L"], spec_kw["budget"]
+    with P.Context(arena_bytes=2 * P.psl_walk_bytes(L, 6912, budget) + (64 << 20), max_walks=2) as ctx:
+        walk = ShardedWalk(ctx, rank, world, torch_exchange(), trace_cap=budget, **spec_kw)
+        n = walk.run()
+        tr = ctx.trace(walk.wid, budget)
+        st = ctx.export_state(walk.wid)
+    q.put((rank, n, tr.tobytes(), st["C"].tobytes(), st["pivot"].tobytes()))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_processes_exchange_through_gloo(P):
+    """Two processes, each a rank with its own context on the GPU, exchanging the partial
+    arrays through a gloo all-reduce on host tensors (no kernel waits on the other process:
+    the exchange happens between launches)."""
+    import socket
+    import torch.multiprocessing as mp
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    spec_kw = dict(L=20011, seed=77, alpha1=4, alpha2=11, budget=5, ls_lmt=2, flip_lmt=6)
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_shard_rank, args=(r, 2, port, q, spec_kw)) for r in range(2)]
+    [p.start() for p in procs]
+    res = sorted(q.get(timeout=600) for _ in procs)
+    [p.join(timeout=120) for p in procs]
+    assert all(p.exitcode == 0 for p in procs)
+    spec = W.WalkSpec(**spec_kw)
+    w = oracle_walk(spec)
+    otr = w.run(spec.budget)
+    for rank, n, tr, C, piv in res:
+        assert n == spec.budget
+        compare_traces(np.frombuffer(tr, dtype=P.TRACE_DTYPE), otr, f"process {rank}")
+        assert np.array_equal(np.frombuffer(C, dtype=np.int32), w.C)
+        assert np.array_equal(np.frombuffer(piv, dtype=np.int8), w.s)
