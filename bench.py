@@ -490,10 +490,7 @@ def run_ours(args):
                        steps_per_graph=G, **hot) as ctx:
             ids = [ctx.submit(s.L, s.seed, s.alpha1, s.alpha2, s.budget) for s in specs]
             ctx.step(args.steps)
-            psl_sum = 0
-            for i in ids:
-                p, seq = ctx.best(i)
-                psl_sum += p
+            psl_best, seqs = ctx.best_many(ids)      # every walk's best sequence, one synchronisation
             h2d, d2h = ctx.transfer_bytes()
         torch.cuda.synchronize(dev)
         dt = time.perf_counter() - t0
@@ -503,7 +500,8 @@ def run_ours(args):
         e2e = {"value": world * flip_evals_rank / float(td.item()), "unit": UNIT,
                "h2d_bytes_per_step": h2d / args.steps, "d2h_bytes_per_step": d2h / args.steps,
                "bytes_counted": "by the library at each host<->device copy (psl_transfer_bytes)",
-               "includes": "submit, walk initialisation, graph capture, steps, status and best-sequence readback"}
+               "includes": "submit, walk initialisation, graph capture, steps, status readback, every walk's best "
+                           "sequence read back (psl_best_many)"}
 
     # the small configuration: L = 1023, one walk from seed 1, N = L, 2000 moves, time to budget
     small = None
@@ -557,13 +555,15 @@ def run_ours(args):
                                "merit_factor_best": float(np.max(mf))}
             Lo, No = specs_o[0].L, specs_o[0].N
             n_hot, hot_ms_o = prof_o.get("hot", (0, 0.0))
-            roof_o = hot_roofline(len(specs_o) * No, Lo, hot_ms_o / max(n_hot, 1), peak, mhz, None)
+            roof_o = hot_roofline(len(specs_o) * No, Lo, hot_ms_o / max(n_hot, 1), peak, mhz,
+                                  stored_counters("k_hot_batched", wl_o.name))
             others[wl_o.name] = {"value": len(specs_o) * No * k_o / (ms_o / 1000.0), "unit": UNIT,
                                  "ms_per_step": ms_o / k_o, "steps": k_o, "graph_steps": k_o,
                                  "hot_kernel": {"threads": tune_o[0], "tile_superblocks": tune_o[1],
                                                 "avg_ms": hot_ms_o / max(n_hot, 1)},
                                  "roofline_frac": roof_o["frac"], "roofline_frac_live_terms": roof_o["frac_live_terms"],
                                  "lookup_ceiling_frac": roof_o["lookup_ceiling"]["frac"],
+                                 "issue_frac": roof_o["issue_frac"], "traffic": roof_o["traffic"],
                                  "init_s": t_init, "description": wl_o.description}
             if quality:
                 others[wl_o.name]["quality"] = quality

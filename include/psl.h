@@ -178,6 +178,12 @@ PSL_API int psl_poll(psl_ctx *ctx, int64_t id, psl_status *out);
  * seq_pm1[0..L-1] its values +-1; cap must be >= L.  PSL_EBUSY while queued. */
 PSL_API int psl_best(psl_ctx *ctx, int64_t id, int32_t *psl, int8_t *seq_pm1, size_t cap);
 
+/* psl_best for n walks at once: psl_out[q] receives the PSL of walk ids[q]'s best sequence
+ * and seqs[q * cap .. q * cap + L - 1] its values +-1 (cap >= the longest L; either output
+ * may be NULL).  The sequences are copied back together with one synchronisation.
+ * PSL_ENOENT / PSL_EBUSY / PSL_EINVAL as psl_best, for the first walk that fails. */
+PSL_API int psl_best_many(psl_ctx *ctx, const int64_t *ids, size_t n, int32_t *psl_out, int8_t *seqs, size_t cap);
+
 /* Frees the walk's slot and device memory.  Running walks are cancelled. */
 PSL_API int psl_release(psl_ctx *ctx, int64_t id);
 

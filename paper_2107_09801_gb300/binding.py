@@ -75,7 +75,7 @@ EXPORTED = ["psl_config_default", "psl_init", "psl_submit", "psl_submit_ex", "ps
             "psl_last_error", "psl_profile", "psl_profile_read", "psl_autotune", "psl_set_hot_config",
             "psl_autocorr_static", "psl_inject_stall", "psl_set_max_sms",
             "psl_best_fitness", "psl_transfer_bytes", "psl_set_steps_per_graph", "psl_alu_peak",
-            "psl_shard_layout", "psl_shard_score", "psl_shard_select", "psl_shard_decide"]
+            "psl_shard_layout", "psl_shard_score", "psl_shard_select", "psl_shard_decide", "psl_best_many"]
 
 _lib = None
 
@@ -124,6 +124,7 @@ def lib():
             "psl_shard_score": (ct.c_int, [P, ct.c_int64, P, ct.c_size_t]),
             "psl_shard_select": (ct.c_int, [P, ct.c_int64, P, P, ct.c_size_t]),
             "psl_shard_decide": (ct.c_int, [P, ct.c_int64, P, ct.c_size_t]),
+            "psl_best_many": (ct.c_int, [P, P, ct.c_size_t, P, P, ct.c_size_t]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -333,6 +334,17 @@ class Context:
 
     def best(self, wid: int):
         return psl_best(self.h, wid, self.L_of[wid])
+
+    def best_many(self, wids) -> tuple[np.ndarray, np.ndarray]:
+        """(PSL of each walk's best sequence, the sequences as rows of +-1 int8, padded with 0
+        to the longest L), copied back together."""
+        wids = np.ascontiguousarray(wids, dtype=np.int64)
+        cap = max((self.L_of.get(int(w), 0) for w in wids), default=0)
+        psl = np.zeros(len(wids), dtype=np.int32)
+        seqs = np.zeros((len(wids), cap), dtype=np.int8)
+        _check(self.h, lib().psl_best_many(self.h, wids.ctypes.data, len(wids), psl.ctypes.data,
+                                           seqs.ctypes.data, cap))
+        return psl, seqs
 
     def release(self, wid: int) -> None:
         psl_release(self.h, wid)

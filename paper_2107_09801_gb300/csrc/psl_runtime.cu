@@ -1082,6 +1082,41 @@ extern "C" int psl_best(psl_ctx *ctx, int64_t id, int32_t *psl_out, int8_t *seq,
   return PSL_OK;
 }
 
+extern "C" int psl_best_many(psl_ctx *ctx, const int64_t *ids, size_t n, int32_t *psl_out, int8_t *seqs,
+                             size_t cap) {
+  if (!ctx || (n && !ids)) return PSL_EINVAL;
+  std::vector<const HostWalk *> ws(n);
+  size_t words_total = 0;
+  for (size_t q = 0; q < n; q++) {
+    const HostWalk *w = find(ctx, ids[q]);
+    if (!w) return fail(ctx, PSL_ENOENT, "unknown walk %lld", (long long)ids[q]);
+    if (w->slot < 0) return fail(ctx, PSL_EBUSY, "walk %lld is queued", (long long)ids[q]);
+    if (seqs && cap < w->p.L) return fail(ctx, PSL_EINVAL, "cap %zu < L %u", cap, w->p.L);
+    ws[q] = w;
+    words_total += (w->p.L + 31) / 32;
+  }
+  if (psl_out)
+    for (size_t q = 0; q < n; q++) psl_out[q] = ctx->h_hdr[ws[q]->slot].psl_best;
+  if (!seqs || n == 0) return PSL_OK;
+  // every walk's packed best sequence copied back in one go, then unpacked on the host
+  std::vector<uint32_t> words(words_total);
+  size_t at = 0;
+  for (size_t q = 0; q < n; q++) {
+    const size_t nw = (ws[q]->p.L + 31) / 32;
+    CK(xfer(ctx, words.data() + at, ctx->h_hdr[ws[q]->slot].bits_best, nw * 4, cudaMemcpyDeviceToHost));
+    at += nw;
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  at = 0;
+  for (size_t q = 0; q < n; q++) {
+    const uint32_t L = ws[q]->p.L;
+    int8_t *out = seqs + q * cap;
+    for (uint32_t i = 0; i < L; i++) out[i] = ((words[at + (i >> 5)] >> (i & 31)) & 1u) ? -1 : 1;
+    at += (L + 31) / 32;
+  }
+  return PSL_OK;
+}
+
 extern "C" int psl_best_fitness(psl_ctx *ctx, int64_t id, uint32_t *value_limbs, double *value, int8_t *seq,
                                 size_t cap) {
   if (!ctx) return PSL_EINVAL;

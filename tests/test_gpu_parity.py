@@ -600,3 +600,21 @@ def test_alu_peak_microbenchmark(P):
     assert all(0 < v <= 128 * 1.02 for v in per_clk.values()), per_clk
     assert per_clk["fadd"] > 32 and per_clk["mix"] > 32 and per_clk["lookup"] > 4, per_clk
     print("lane-ops (lookups) per SM per clock:", per_clk)
+
+
+def test_best_many_matches_best(P):
+    specs = W.small_specs(seed=41, count=7, L_choices=(13, 255, 1000, 4095))
+    with P.Context(arena_bytes=ARENA, max_walks=16) as ctx:
+        ids = [submit_spec(ctx, s, trace=False) for s in specs]
+        ctx.run()
+        d0 = ctx.transfer_bytes()[1]
+        psl, seqs = ctx.best_many(ids)
+        assert ctx.transfer_bytes()[1] - d0 == sum(4 * ((s.L + 31) // 32) for s in specs)
+        for q, (i, s) in enumerate(zip(ids, specs)):
+            p1, seq1 = ctx.best(i)
+            assert psl[q] == p1 and np.array_equal(seqs[q, :s.L], seq1) and not seqs[q, s.L:].any()
+            w = oracle_walk(s)
+            w.run(s.budget)
+            assert psl[q] == w.psl_best and np.array_equal(seqs[q, :s.L], w.sol_best)
+        with pytest.raises(P.PslError):
+            ctx.best_many(ids + [12345])
