@@ -86,7 +86,8 @@ typedef struct {
   int32_t max_walks;        /* number of walk slots                                   */
   int32_t hot_tile_sb;      /* k-tile of the batched kernel in super-blocks of 30 k: 16 or 32; 0 = auto */
   int32_t steps_per_graph;  /* steps captured per CUDA graph launch; 0 = plain launches */
-  int32_t hot_threads;      /* neighbours per block of the batched kernel: 128, 256 or 512; 0 = auto */
+  int32_t hot_threads;      /* neighbours per block of the batched kernel: 128, 256 or 512; or 448 / 896
+                               for the producer / consumer form (with hot_tile_sb 16 / 32); 0 = auto */
   int32_t max_sms;          /* SMs' worth of resident blocks the persistent kernels launch (0 = all);
                                lets contexts on different streams share the GPU side by side */
 } psl_config;
@@ -259,7 +260,9 @@ PSL_API int psl_alu_peak(int32_t device, void *stream, psl_alu_peak_t *out);
 
 /* Autotuner of the batched form: admits queued walks, then times every supported
  * configuration of the neighbourhood kernel (neighbours per block 128/256/512 x k-tile
- * of 16/32 super-blocks, which sets the shared-memory footprint) on the walks now
+ * of 16/32 super-blocks, which sets the shared-memory footprint, and the producer /
+ * consumer form: 448 x 16, 896 x 32, where two producer warps stage and build each tile's
+ * tables into one of two buffers while the other warps score) on the walks now
  * running, reps launches each, and keeps the fastest for this context.  The timed
  * launches only recompute window scores that the next step recomputes, so no result
  * changes.  Returns threads | (tile_sb << 16) of the choice, PSL_ESTATE when no walk

@@ -723,6 +723,370 @@ __global__ void __launch_bounds__(kPlainThreads, 1) k_hot_plain(WalkDev *hdrp) {
   W.pslj[i - 1] = pj;
 }
 
+// ------------------------------------------------------------------------------------
+// neighbourhood score, producer / consumer form
+//
+// The same scoring as k_hot_batched, with the per-tile block barriers taken out of the
+// scoring loop: two producer warps stage each k-tile's per-k values (TMA bulk copy) and
+// build its tables into one of two buffers, while NWS scorer warps score the previous
+// tile from the other buffer.  Per buffer, "full" (the producer arrives once the tables are
+// built) and "empty" (every scorer warp arrives once it has scored from the buffer)
+// mbarriers order the two sides; a scorer warp never waits for another scorer warp, so the
+// warps of a block drift up to one tile apart instead of meeting at every tile.  Every wait
+// is bounded; a wait that runs out marks the walk failed and the block stops.  The
+// producer derives the block's kin/kout range (which tables a tile needs) from the item's
+// window positions directly: they are consecutive modulo L, and kin (kout) rises (falls) to
+// the middle of the sequence, so the extremes lie at the ends or at the middle.
+// ------------------------------------------------------------------------------------
+constexpr int kPcProducerWarps = 2;
+constexpr uint32_t kPcEnd = 0xffffffffu;
+enum PcFlags : uint32_t { kPcFirst = 1, kPcLast = 2, kPcEmpty = 4, kPcSkip = 8 };
+
+struct PcTile {       // the tile a buffer holds, written by the producer before it arrives on "full"
+  uint32_t item;      // work item, or kPcEnd
+  int32_t kt0;        // first shift of the tile
+  uint32_t flags;     // kPcFirst / kPcLast: first / last tile of the item; kPcEmpty: nothing to score;
+                      // kPcSkip: the walk is not running (or failed): nothing to write either
+  uint32_t pad;
+};
+
+template <int NSB, bool MB>
+constexpr size_t pc_smem_bytes() {
+  return 2 * (size_t)NSB * TabLayout<MB>::SBB + 2 * (size_t)NSB * kSbK * 16 + 128;
+}
+size_t hot_pc_smem(uint32_t nsb, bool masked) {
+  return 2 * (size_t)nsb * (masked ? TabLayout<true>::SBB : TabLayout<false>::SBB) + 2 * (size_t)nsb * kSbK * 16 + 128;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+__device__ __forceinline__ void producer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(32 * kPcProducerWarps) : "memory"); }
+
+__device__ __forceinline__ int pc_kin(int j, int L) { return min(j, L - 1 - j); }
+__device__ __forceinline__ int pc_kout(int j, int L) { return max(j, L - 1 - j); }
+
+// kin / kout extremes over positions x..y (x <= y, no wrap)
+__device__ __forceinline__ void pc_seg(int x, int y, int L, int &kin_lo, int &kin_hi, int &kout_lo, int &kout_hi) {
+  const int c1 = min(max((L - 1) / 2, x), y), c2 = min(max(L / 2, x), y);
+  kin_lo = min(kin_lo, min(pc_kin(x, L), pc_kin(y, L)));
+  kin_hi = max(kin_hi, max(max(pc_kin(x, L), pc_kin(y, L)), max(pc_kin(c1, L), pc_kin(c2, L))));
+  kout_hi = max(kout_hi, max(pc_kout(x, L), pc_kout(y, L)));
+  kout_lo = min(kout_lo, min(min(pc_kout(x, L), pc_kout(y, L)), min(pc_kout(c1, L), pc_kout(c2, L))));
+}
+
+template <int NWS, int NSB, int FB>
+__global__ void __launch_bounds__(32 * (NWS + kPcProducerWarps), NWS <= 14 ? 2 : 1) k_hot_pc(WalkDev *hdr, const HotItem *items,
+                                                                              Schedule *sched) {
+  static_assert(NSB <= 32, "the per-super-block swizzle assumes at most 32 super-blocks per tile");
+  constexpr bool MB = FB == 4;
+  constexpr int NT = 32 * NWS;  // window positions per item
+  constexpr int SBB = TabLayout<MB>::SBB, SBF = TabLayout<MB>::SBF;
+  constexpr int kTileK = NSB * kSbK;
+  extern __shared__ __align__(128) float smem_pc[];
+  __shared__ __align__(8) uint64_t s_bar[6];  // full[2], empty[2], copy[2]
+  __shared__ PcTile s_hdr[2];
+  __shared__ uint32_t s_item;
+  __shared__ int s_err, s_pflag, s_prun, s_pstall;
+  const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(smem_pc);
+  const uint32_t tab_s0 = (raw_s + 127u) & ~127u;
+  float *tab0 = smem_pc + (tab_s0 - raw_s) / 4;
+  float4 *stage0 = reinterpret_cast<float4 *>(tab0 + 2 * NSB * SBF);
+  const uint32_t stage_s0 = tab_s0 + 2 * NSB * SBB;
+  const uint32_t bar_s = (uint32_t)__cvta_generic_to_shared(s_bar);
+  auto full_b = [&](int b) { return bar_s + 8u * (uint32_t)b; };
+  auto empty_b = [&](int b) { return bar_s + 16u + 8u * (uint32_t)b; };
+  auto copy_b = [&](int b) { return bar_s + 32u + 8u * (uint32_t)b; };
+  const int warp = (int)(threadIdx.x >> 5), lane = (int)(threadIdx.x & 31);
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; b++) {
+      mbar_init(full_b(b), 1);
+      mbar_init(empty_b(b), NWS);
+      mbar_init(copy_b(b), 1);
+    }
+    fence_mbar_init();
+    s_err = 0;
+  }
+  if constexpr (MB) {  // masked lookups with an empty mask read entry 0: zero tables, builds keep it 0
+    for (int q = threadIdx.x; q < 2 * NSB * SBF; q += blockDim.x) tab0[q] = 0.f;
+  }
+  __syncthreads();
+
+  if (warp >= NWS) {
+    // ---------------------------------- producer ----------------------------------
+    const int ptid = (int)threadIdx.x - 32 * NWS;
+    uint32_t s = 0;                 // tile sequence number (buffer s & 1, use s >> 1)
+    uint32_t ncopy0 = 0u, ncopy1 = 0u;  // copies issued into each staging buffer
+    bool ok = true;
+    // A bounded wait decided by producer thread 0 and shared with the other producer thread(s),
+    // so that both producer warps always take the same branch (they meet at named barriers);
+    // after a success each thread observes the completed phase itself (at once).
+    auto pwait = [&](uint32_t mbar, uint32_t parity, int limit) {
+      if (ptid == 0) s_pflag = mbar_wait_bounded(mbar, parity, limit) ? 1 : 0;
+      producer_sync();
+      const bool r = s_pflag != 0;
+      if (r && ptid != 0) mbar_wait_bounded(mbar, parity, 1 << 20);
+      producer_sync();  // s_pflag is free for the next wait
+      return r;
+    };
+    // hands tile s over to the scorers: waits until they have released its buffer
+    auto publish = [&](uint32_t item, int kt0, uint32_t flags) {
+      const int b = (int)(s & 1u);
+      if (ptid == 0) {
+        s_hdr[b].item = item;
+        s_hdr[b].kt0 = kt0;
+        s_hdr[b].flags = flags;
+        mbar_arrive(full_b(b));  // release: the tables and the header are visible to the scorers
+      }
+      s++;
+    };
+    auto claim = [&]() {  // buffer s & 1 is free once every scorer warp released its use before
+      const int b = (int)(s & 1u);
+      if (s >= 2 && !pwait(empty_b(b), ((s >> 1) - 1u) & 1u, 1 << 20)) return false;
+      return true;
+    };
+    for (;;) {
+      // thread 0 takes the next item and reads the walk's state once for both producer warps
+      if (ptid == 0) {
+        const uint32_t nx = atomicAdd(&sched->hot_next, 1u);
+        s_item = nx;
+        s_prun = 0, s_pstall = 0;
+        if (nx < sched->nitems) {
+          const WalkDev &Wn = hdr[items[nx].slot];
+          s_prun = Wn.status == kRunning ? 1 : 0;
+          s_pstall = Wn.inject_stall ? 1 : 0;
+        }
+      }
+      producer_sync();
+      const uint32_t item = s_item;
+      const bool run = s_prun != 0, stall = s_pstall != 0;
+      producer_sync();  // every producer thread has read them before thread 0 writes the next
+      if (item >= sched->nitems) break;
+      const HotItem it = items[item];
+      WalkDev &W = hdr[it.slot];
+      if (!run) {
+        if (!(ok = claim())) break;
+        publish(item, 0, kPcFirst | kPcLast | kPcEmpty | kPcSkip);
+        continue;
+      }
+      const int L = (int)W.L, N = (int)W.N;
+      // the item's positions: start + i0 .. start + min(i0 + NT - 1, N), modulo L
+      const int a = (int)(((uint64_t)W.start + (uint64_t)it.i0) % (uint64_t)L);
+      const int cnt = min((int)it.i0 + NT - 1, N) - (int)it.i0 + 1;
+      int kin_lo = INT_MAX, kin_hi = 0, kout_lo = INT_MAX, kout_hi = 0;
+      if (a + cnt - 1 < L) {
+        pc_seg(a, a + cnt - 1, L, kin_lo, kin_hi, kout_lo, kout_hi);
+      } else {
+        pc_seg(a, L - 1, L, kin_lo, kin_hi, kout_lo, kout_hi);
+        pc_seg(0, a + cnt - 1 - L, L, kin_lo, kin_hi, kout_lo, kout_hi);
+      }
+      const int kmax = kout_hi;
+      const int tiles_per_chunk = (int)W.kchunk_sb / NSB;
+      const int tile_lo = item_tile_lo<NSB>(W, it);
+      const int tile_hi = W.ksplit > 1 ? min((kmax + kTileK - 1) / kTileK, tile_lo + tiles_per_chunk)
+                                       : (kmax + kTileK - 1) / kTileK;
+      const int ntiles = max(0, tile_hi - tile_lo);
+      if (ntiles == 0) {
+        if (!(ok = claim())) break;
+        publish(item, 0, kPcFirst | kPcLast | kPcEmpty);
+        continue;
+      }
+      bool failed = false;
+      for (int tile = 0; tile < ntiles; tile++) {
+        const int kt0 = 1 + (tile_lo + tile) * kTileK;
+        const uint32_t flags = (tile == 0 ? kPcFirst : 0u) | (tile + 1 == ntiles ? kPcLast : 0u);
+        if (!(ok = claim())) break;
+        const int b = (int)(s & 1u);
+        if (failed) {  // the walk failed on an earlier tile of this item: hand the rest over unscored
+          publish(item, kt0, flags | kPcEmpty | kPcSkip);
+          continue;
+        }
+        // stage the tile's per-k values (the test hook issues nothing and waits briefly)
+        if (ptid == 0 && !stall) {
+          const uint32_t bytes = 16u * (uint32_t)min(kTileK, L - kt0);
+          fence_proxy_async();
+          mbar_expect_tx(copy_b(b), bytes);
+          tma_load_1d(stage_s0 + (uint32_t)b * (kTileK * 16), W.T + kt0, bytes, copy_b(b));
+        }
+        if (!stall) (b ? ncopy1 : ncopy0)++;
+        const uint32_t nc = b ? ncopy1 : ncopy0;
+        // copy nc of this buffer completes its phase nc - 1; with no copy issued, the phase in
+        // progress (parity nc) never completes and the short wait runs out
+        const bool got = stall ? pwait(copy_b(b), nc & 1u, 64) : pwait(copy_b(b), (nc - 1u) & 1u, 1 << 20);
+        if (!got) {
+          if (!stall) {  // a copy that may still be in flight: stop using this block
+            ok = false;
+            if (ptid == 0) {
+              W.error = (uint32_t)-5;  // PSL_ETIMEOUT of the library header
+              W.status = kError;
+            }
+            break;
+          }
+          // nothing is in flight: the walk fails, the block carries on
+          if (ptid == 0) {
+            W.error = (uint32_t)-5;
+            W.status = kError;
+          }
+          failed = true;
+          publish(item, kt0, flags | kPcEmpty | kPcSkip);
+          continue;
+        }
+        // build the tile's tables (one group per producer thread at a time)
+        const float4 *Ts = stage0 + b * kTileK;
+        for (int g = ptid; g < 6 * NSB; g += 32 * kPcProducerWarps) {
+          const int sb = g % NSB, q = g / NSB;
+          const int ka = kt0 + sb * kSbK;
+          const bool need_w = ka <= kin_hi;
+          const bool need_e = ka + kSbK - 1 > kin_lo && ka <= kmax;
+          const bool need_m = MB && ((ka <= kin_hi && ka + kSbK - 1 >= kin_lo - 4) ||
+                                     (ka <= kmax && ka + kSbK - 1 >= kout_lo - 4));
+          if (need_w || need_e) build_group<MB>(tab0 + b * NSB * SBF, sb, q, Ts, kt0, ka + 5 * q, L, need_w, need_e, need_m);
+        }
+        producer_sync();  // every table of the tile is written
+        publish(item, kt0, flags);
+      }
+      if (!ok) break;
+    }
+    // end of work (or a stopped block): the scorers leave at the next header
+    if (ok && claim()) {
+      publish(kPcEnd, 0, 0);
+    } else if (ptid == 0) {
+      s_err = 1;
+      // release the scorers waiting on either buffer; they read kPcEnd and leave
+      for (int b = 0; b < 2; b++) {
+        s_hdr[b].item = kPcEnd;
+        mbar_arrive(full_b(b));
+      }
+    }
+    return;
+  }
+
+  // ---------------------------------- scorers ----------------------------------
+  uint32_t s = 0;
+  // state of the item in progress (lane = one window position)
+  uint32_t cur = kPcEnd;
+  WalkDev *Wp = nullptr;
+  int i = 0, j = 0, kin = 0, kout = 0, L = 0, N = 0;
+  bool live = false, plus_side = false, skip = false;
+  uint32_t M = 0;
+  WarpRange wr{0, 0, 0, 0};
+  float hi = 0.f, lo = 0.f, a0 = 0.f, a1 = 0.f;
+  for (;;) {
+    const int b = (int)(s & 1u);
+    // one decision for the whole warp (a lane whose wait ran out fails every lane)
+    const bool got = mbar_wait_bounded(full_b(b), (s >> 1) & 1u);
+    if (__any_sync(0xffffffffu, !got)) {
+      if (lane == 0) s_err = 1;
+      if (cur != kPcEnd && lane == 0 && Wp) {
+        Wp->error = (uint32_t)-5;
+        Wp->status = kError;
+      }
+      break;
+    }
+    const PcTile h = s_hdr[b];
+    if (h.item == kPcEnd) break;
+    if (h.flags & kPcFirst) {
+      cur = h.item;
+      const HotItem it = items[cur];
+      Wp = hdr + it.slot;
+      skip = (h.flags & kPcSkip) != 0;
+      hi = lo = a0 = a1 = 0.f;
+      if (!skip) {
+        const WalkDev &W = *Wp;
+        L = (int)W.L, N = (int)W.N;
+        i = (int)it.i0 + 32 * warp + lane;
+        live = i <= N;
+        j = (int)(((uint64_t)W.start + (uint64_t)min(i, N)) % (uint64_t)L);
+        const bool warp_live = (int)it.i0 + 32 * warp <= N;
+        kin = min(j, L - 1 - j), kout = max(j, L - 1 - j);
+        plus_side = j < L - 1 - j;
+        M = getbit(W.bits, j) ? 0xffffffffu : 0u;
+        wr.kin_lo = __reduce_min_sync(0xffffffffu, kin);
+        wr.kin_hi = __reduce_max_sync(0xffffffffu, kin);
+        wr.kout_lo = __reduce_min_sync(0xffffffffu, kout);
+        wr.kout_hi = warp_live ? __reduce_max_sync(0xffffffffu, kout) : 0;
+      }
+    }
+    if (h.flags & kPcSkip) skip = true;
+    if (!(h.flags & kPcEmpty) && !skip) {
+      const WalkDev &W = *Wp;
+      const uint32_t *__restrict__ win_f = W.win_f;
+      const uint32_t *__restrict__ win_r = W.win_r;
+      const int kt0 = h.kt0;
+      const float4 *Ts = stage0 + b * kTileK;
+      const int n_all = sb_count(wr.kout_hi, kt0, 0, NSB);
+      const int n_int = min(sb_count(wr.kin_lo, kt0, kSbK - 1, NSB), n_all);
+      const int e0 = max(n_int, min(n_all, sb_count(wr.kin_hi, kt0, 0, NSB)));
+      const int n_edge = max(e0, min(n_all, sb_count(wr.kout_lo, kt0, kSbK - 1, NSB)));
+      const uint32_t bsw0 = tab_s0 + (uint32_t)b * (NSB * SBB);
+      int sb = 0;
+      {
+        const uint32_t *wu = win_f + (j + kt0), *wv = win_r + (j - kt0);
+        uint32_t bsw = bsw0;
+        for (; sb + FB - 1 < n_int; sb += FB) {
+#pragma unroll
+          for (int u = 0; u < FB; u++) sb_interior<MB>(a0, a1, wu + u * kSbK, wv - u * kSbK, M, bsw + u * (SBB + 4));
+          flush2(hi, lo, a0, a1);
+          wu += FB * kSbK, wv -= FB * kSbK, bsw += FB * (SBB + 4);
+        }
+        if (sb < n_int) {
+          for (; sb < n_int; sb++) {
+            sb_interior<MB>(a0, a1, wu, wv, M, bsw);
+            wu += kSbK, wv -= kSbK, bsw += SBB + 4;
+          }
+          flush2(hi, lo, a0, a1);
+        }
+      }
+      for (; sb < e0; sb++) {
+        sb_generic<MB>(a0, a1, win_f, win_r, Ts, kt0, j, kt0 + sb * kSbK, kin, kout, plus_side, M,
+                       bsw0 + sb * (SBB + 4), L, wr);
+        flush2(hi, lo, a0, a1);
+      }
+      {
+        const int step = plus_side ? kSbK : -kSbK;
+        const uint32_t *we = plus_side ? win_f + (j + kt0 + sb * kSbK) : win_r + (j - kt0 - sb * kSbK);
+        uint32_t bsw = bsw0 + sb * (SBB + 4);
+        for (; sb + FB - 1 < n_edge; sb += FB) {
+#pragma unroll
+          for (int u = 0; u < FB; u++) sb_edge<MB>(a0, a1, we + u * step, M, bsw + u * (SBB + 4));
+          flush2(hi, lo, a0, a1);
+          we += FB * step, bsw += FB * (SBB + 4);
+        }
+        if (sb < n_edge) {
+          for (; sb < n_edge; sb++) {
+            sb_edge<MB>(a0, a1, we, M, bsw);
+            we += step, bsw += SBB + 4;
+          }
+          flush2(hi, lo, a0, a1);
+        }
+      }
+      for (; sb < n_all; sb++) {
+        sb_generic<MB>(a0, a1, win_f, win_r, Ts, kt0, j, kt0 + sb * kSbK, kin, kout, plus_side, M,
+                       bsw0 + sb * (SBB + 4), L, wr);
+        flush2(hi, lo, a0, a1);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty_b(b));  // this warp is done with the buffer
+    if ((h.flags & kPcLast) && !skip && live) {
+      WalkDev &W = *Wp;
+      const HotItem it = items[cur];
+      if (W.ksplit > 1) {
+        W.score_part[(size_t)it.kc * N + (i - 1)] = hi + lo;
+      } else {
+        W.score[i - 1] = hi + lo;
+      }
+      if (W.ksplit <= 1 || it.kc == W.kc_psl) {
+        // exact neighbour PSL, only when some neighbour may beat psl_best
+        int pj = INT_MAX;
+        if (W.ktau_on) pj = neighbour_psl(W, W.ktau, (int)W.nktau, j, L, M ? -1 : 1, W.psl - 8, 0);
+        W.pslj[i - 1] = pj;
+      }
+    }
+    s++;
+  }
+}
+
 static uint32_t g_hot_blocks_per_sm[3][2][2];  // occupancy of every variant, measured at set-up
 
 using HotFn = void (*)(WalkDev *, const HotItem *, Schedule *);
@@ -740,7 +1104,23 @@ static HotFn hot_variant(uint32_t threads, uint32_t tile_sb, uint32_t flush_sb) 
   return flush_sb == 4 ? hot_variant_fb<4>(threads, tile_sb) : hot_variant_fb<8>(threads, tile_sb);
 }
 
+// Producer / consumer configurations: hot_threads is the number of window positions per work
+// item (the scorer lanes); 896 = 28 scorer warps, one block per SM, 32-super-block tiles for
+// long walks; 448 = 14 scorer warps, two blocks per SM, 16-super-block tiles.  Short-walk
+// batches (five tables per group) use 16-super-block tiles in both.
+static bool is_pc(uint32_t threads) { return threads == 896 || threads == 448; }
+
+static HotFn pc_variant(uint32_t threads, uint32_t fb) {
+  if (threads == 896) return fb == 4 ? k_hot_pc<28, 16, 4> : k_hot_pc<28, 32, 8>;
+  return fb == 4 ? k_hot_pc<14, 16, 4> : k_hot_pc<14, 16, 8>;
+}
+
+static uint32_t pc_nsb(uint32_t threads, uint32_t fb) { return (threads == 896 && fb == 8) ? 32u : 16u; }
+
+static uint32_t g_pc_blocks_per_sm[2][2];  // [448 / 896][fb 4 / 8]
+
 bool hot_config_supported(uint32_t threads, uint32_t tile_sb) {
+  if (is_pc(threads)) return tile_sb == (threads == 896 ? 32u : 16u);
   return (threads == 128 || threads == 256 || threads == 512) && (tile_sb == 16 || tile_sb == 32);
 }
 
@@ -762,11 +1142,28 @@ cudaError_t prepare_hot_kernels() {
         if (e != cudaSuccess) return e;
         g_hot_blocks_per_sm[variant_index(t)][sb == 32 ? 1 : 0][fb == 8 ? 1 : 0] = (uint32_t)(nb > 0 ? nb : 1);
       }
+  for (uint32_t t : {448u, 896u})
+    for (uint32_t fb : {4u, 8u}) {
+      HotFn f = pc_variant(t, fb);
+      const size_t smem = hot_pc_smem(pc_nsb(t, fb), fb == 4);
+      cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+      int nb = 0;
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, f, (int)(t + 32 * kPcProducerWarps), smem);
+      if (e != cudaSuccess) return e;
+      g_pc_blocks_per_sm[t == 896 ? 1 : 0][fb == 8 ? 1 : 0] = (uint32_t)(nb > 0 ? nb : 1);
+    }
   return cudaSuccess;
 }
 
 cudaError_t launch_hot_batched(const LaunchCtx &c) {
   const uint32_t fb = c.hot_flush_sb == 4 ? 4u : 8u;
+  if (is_pc(c.hot_threads)) {
+    const uint32_t per_sm = g_pc_blocks_per_sm[c.hot_threads == 896 ? 1 : 0][fb == 8 ? 1 : 0];
+    pc_variant(c.hot_threads, fb)<<<per_sm * c.sm_count, c.hot_threads + 32 * kPcProducerWarps,
+                                    hot_pc_smem(pc_nsb(c.hot_threads, fb), fb == 4), c.stream>>>(c.hdr, c.items, c.sched);
+    return cudaGetLastError();
+  }
   const uint32_t per_sm = g_hot_blocks_per_sm[variant_index(c.hot_threads)][c.hot_tile_sb == 32 ? 1 : 0][fb == 8 ? 1 : 0];
   hot_variant(c.hot_threads, c.hot_tile_sb, fb)<<<per_sm * c.sm_count, c.hot_threads,
                                                   hot_batched_smem(c.hot_tile_sb, fb == 4), c.stream>>>(c.hdr, c.items, c.sched);

@@ -1273,8 +1273,11 @@ extern "C" int psl_autotune(psl_ctx *ctx, int reps) {
   CK(cudaEventCreate(&b));
   float best_ms = 3.4e38f;
   int32_t best_t = ctx->cfg.hot_threads, best_sb = ctx->cfg.hot_tile_sb;
-  for (int32_t t : {128, 256, 512})
-    for (int32_t sb : {16, 32}) {
+  const int32_t configs[8][2] = {{128, 16}, {128, 32}, {256, 16}, {256, 32}, {512, 16}, {512, 32},
+                                 {448, 16}, {896, 32}};  // the last two: producer / consumer form
+  for (const auto &cf : configs) {
+    {
+      const int32_t t = cf[0], sb = cf[1];
       ctx->cfg.hot_threads = t;
       ctx->cfg.hot_tile_sb = sb;
       if ((rc = rebuild_active(ctx))) return rc;
@@ -1293,6 +1296,7 @@ extern "C" int psl_autotune(psl_ctx *ctx, int reps) {
       CK(cudaEventElapsedTime(&ms, a, b));
       if (ms < best_ms) best_ms = ms, best_t = t, best_sb = sb;
     }
+  }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
   ctx->cfg.hot_threads = best_t;

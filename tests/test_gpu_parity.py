@@ -358,7 +358,8 @@ def test_argument_errors(P):
 # ------------------------------------------------------------------------------------------------
 # configurations of the neighbourhood kernel and the autotuner leave every decision unchanged
 # ------------------------------------------------------------------------------------------------
-@pytest.mark.parametrize("threads,tile_sb", [(128, 16), (128, 32), (256, 16), (512, 16), (512, 32)])
+@pytest.mark.parametrize("threads,tile_sb", [(128, 16), (128, 32), (256, 16), (512, 16), (512, 32), (448, 16),
+                                             (896, 32)])
 def test_hot_kernel_configurations_match_oracle(P, threads, tile_sb):
     specs = W.small_specs(seed=21, count=6, L_choices=(63, 1000, 2047, 4095))
     res = run_gpu(P, specs, hot_threads=threads, hot_tile_sb=tile_sb)
@@ -366,6 +367,21 @@ def test_hot_kernel_configurations_match_oracle(P, threads, tile_sb):
         w = oracle_walk(spec)
         compare_traces(tr, w.run(spec.budget), f"{threads}/{tile_sb} L={spec.L}")
         compare_final_state(st, w)
+
+
+@pytest.mark.parametrize("threads,tile_sb", [(512, 32), (448, 16), (896, 32)])
+def test_hot_kernel_configurations_long_walks(P, threads, tile_sb):
+    """Walks of L >= 4096 (the long-walk kernel variants), alone (k range split over blocks)
+    and in a batch, in the regular and the producer / consumer forms."""
+    specs = [W.WalkSpec(L=L, seed=80 + L, alpha1=a1, alpha2=a2, budget=b, n_lmt=nl, ls_lmt=2, flip_lmt=5)
+             for L, a1, a2, b, nl in ((4096, 4, 13, 12, 6912), (9001, 3, 10, 10, 900), (20011, 4, 13, 8, 6912),
+                                      (70001, 2, 11, 4, 6912))]
+    for group in (specs, specs[-1:]):
+        res = run_gpu(P, group, hot_threads=threads, hot_tile_sb=tile_sb)
+        for spec, (tr, st, _, _) in zip(group, res):
+            w = oracle_walk(spec)
+            compare_traces(tr, w.run(spec.budget), f"{threads}/{tile_sb} L={spec.L}")
+            compare_final_state(st, w)
 
 
 def test_autotune_keeps_results(P, tmp_path):
@@ -396,10 +412,11 @@ def test_single_long_walk_k_split(P):
 # ------------------------------------------------------------------------------------------------
 # failure path: a bounded device wait that runs out ends one walk, not the context
 # ------------------------------------------------------------------------------------------------
-def test_bounded_wait_timeout_marks_only_that_walk(P):
+@pytest.mark.parametrize("hot", [(256, 32), (896, 32), (448, 16)])
+def test_bounded_wait_timeout_marks_only_that_walk(P, hot):
     specs = [W.WalkSpec(L=L, seed=40 + r, alpha1=3, alpha2=9, budget=12, ls_lmt=4)
-             for r, L in enumerate([1023, 2047, 4095])]
-    with P.Context(arena_bytes=ARENA, max_walks=8) as ctx:
+             for r, L in enumerate([1023, 2047, 4095, 5000])]
+    with P.Context(arena_bytes=ARENA, max_walks=8, hot_threads=hot[0], hot_tile_sb=hot[1]) as ctx:
         ids = [submit_spec(ctx, s) for s in specs]
         ctx.step(2)
         ctx.inject_stall(ids[1])
@@ -407,7 +424,7 @@ def test_bounded_wait_timeout_marks_only_that_walk(P):
         st = [ctx.poll(i) for i in ids]
         assert st[1]["state"] == P.PSL_ERROR and st[1]["error"] == -5       # PSL_ETIMEOUT
         assert st[1]["moves"] == 2
-        for k in (0, 2):
+        for k in (0, 2, 3):
             assert st[k]["state"] == P.PSL_DONE
             w = oracle_walk(specs[k])
             compare_traces(ctx.trace(ids[k], specs[k].budget), w.run(specs[k].budget), f"L={specs[k].L}")
