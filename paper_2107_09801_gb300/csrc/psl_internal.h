@@ -113,7 +113,9 @@ struct Schedule {
   uint32_t max_chunk_apply;  // most update-pass chunks of any listed walk
   uint32_t max_chunk_rc;     // most re-check chunks of any listed walk
   uint32_t hot_next;         // next neighbourhood item to hand out (reset by k_decide)
-  uint32_t pad[3];
+  uint32_t general;          // some listed walk needs the general update pass (initialisation or a phase
+                             // switch): set by the host and by k_decide, cleared by k_select
+  uint32_t pad[2];
 };
 
 struct LaunchCtx {

@@ -435,6 +435,7 @@ __global__ void __launch_bounds__(256) k_apply_move(WalkDev *hdr, const uint32_t
 
 // persistent grid over (walk, chunk) pairs of the schedule
 __global__ void __launch_bounds__(256) k_apply(WalkDev *hdr, const uint32_t *active, const Schedule *sched) {
+  if (!sched->general) return;  // every walk's step was an ordinary move: k_apply_move did it all
   const uint32_t nch = sched->max_chunk_apply, V = sched->nactive * nch;
   for (uint32_t v = blockIdx.x; v < V; v += gridDim.x) {
     __syncthreads();  // shared reduction buffers of the previous pair are free
@@ -682,8 +683,9 @@ __device__ __forceinline__ void select_warp(WalkDev &W) {
 }
 
 // Windows above kSelectWarpN neighbours take a block each; the rest a warp each.
-__global__ void __launch_bounds__(1024) k_select(WalkDev *hdr, const uint32_t *active, const Schedule *sched) {
+__global__ void __launch_bounds__(1024) k_select(WalkDev *hdr, const uint32_t *active, Schedule *sched) {
   const uint32_t nact = sched->nactive;
+  if (blockIdx.x == 0 && threadIdx.x == 0) sched->general = 0;  // k_decide sets it again for a phase switch
   for (uint32_t a = blockIdx.x; a < nact; a += gridDim.x) {
     WalkDev &W = hdr[active[a]];
     if ((int)W.N <= kSelectWarpN) continue;  // the same reading in every thread of the block
@@ -1018,7 +1020,9 @@ __global__ void __launch_bounds__(256) k_decide(WalkDev *hdr, const uint32_t *ac
   if (blockIdx.x == 0 && threadIdx.x == 0) sched->hot_next = 0;
   for (uint32_t a = blockIdx.x; a < sched->nactive; a += gridDim.x) {
     __syncthreads();
-    decide_one(hdr[active[a]]);
+    WalkDev &W = hdr[active[a]];
+    decide_one(W);
+    if (threadIdx.x == 0 && W.mode == kModeSwitch) sched->general = 1;  // the next update pass needs k_apply
   }
 }
 

@@ -640,6 +640,7 @@ static int rebuild_active(psl_ctx *ctx) {
   sc.max_chunk_apply = ctx->max_chunk_apply;
   sc.max_chunk_rc = ctx->max_chunk_rc;
   sc.hot_next = 0;
+  sc.general = 1;
   CK(xfer(ctx, ctx->d_sched, &sc, sizeof sc, cudaMemcpyHostToDevice));
   CK(cudaStreamSynchronize(ctx->stream));  // h_pinned and sc are reused / temporaries
   ctx->active_dirty = false;
@@ -665,6 +666,7 @@ static int upload_schedule(psl_ctx *ctx, Schedule *d, uint32_t nactive, uint32_t
   sc.nactive = nactive;
   sc.max_chunk_apply = apply_chunks;
   sc.max_chunk_rc = rc_chunks;
+  sc.general = 1;  // initialisation and the plain form run the general update pass every time
   CK(xfer(ctx, d, &sc, sizeof sc, cudaMemcpyHostToDevice));
   CK(cudaStreamSynchronize(ctx->stream));
   return PSL_OK;
