@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--alpha2-tables", action="store_true",
+                    help="score alpha = 2 batches with the subset-sum tables instead of the closed form")
     ap.add_argument("--other-configs", type=int, default=1, help="also time the L=16383 x 4096 and L=1048575 x 148 batches")
     ap.add_argument("--serving", type=int, default=100,
                     help="requests of the serving trace run at 0.8x the capacity measured by the probe (0: skip)")
@@ -217,13 +219,23 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
-def kernel_source_hash() -> str:
-    """Hash of the sources of the neighbourhood kernel (its translation unit and headers)."""
+def kernel_source_hash(kernel: str = "k_hot_batched") -> str:
+    """Hash of the sources of a neighbourhood kernel (its translation unit and headers)."""
     h = hashlib.sha256()
-    for fn in ("psl_hot.cu", "psl_device.cuh"):
+    tu = "psl_alpha2.cu" if kernel.startswith("k_hot_alpha2") else "psl_hot.cu"
+    for fn in (tu, "psl_device.cuh"):
         with open(os.path.join(ROOT, "paper_2107_09801_gb300", "csrc", fn), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
+
+
+def plane_steps_per_flip_eval(L: int, psls) -> float:
+    """Bit-plane steps (logic op, population count, add) of the alpha = 2 closed form per
+    flip-eval, averaged over the neighbour position: P = bitlen(PSL) + 1 planes for each of the
+    about (L-1)/32 + 1 forward and backward words, and one step per word of the
+    min(j, L-1-j) shifts of the partner-product term."""
+    P = float(np.mean([int(p).bit_length() + 1 for p in psls])) if len(psls) else 1.0
+    return P * ((L - 1) / 32.0 + 1.0) + (L / 4.0) / 32.0
 
 
 def stored_counters(kernel: str, workload: str):
@@ -233,7 +245,7 @@ def stored_counters(kernel: str, workload: str):
     try:
         d = json.load(open(p))
         rec = d[kernel][workload]
-        if rec.get("source_hash") == kernel_source_hash():
+        if rec.get("source_hash") == kernel_source_hash(kernel):
             return rec
     except Exception:
         pass
@@ -308,7 +320,8 @@ def measure_alu_peak(local: int, stream) -> dict:
     return pk
 
 
-def hot_roofline(walks_x_N: int, L: int, hot_avg_ms: float, peak: dict, mhz_run: float, counters) -> dict:
+def hot_roofline(walks_x_N: int, L: int, hot_avg_ms: float, peak: dict, mhz_run: float, counters,
+                 kernel: str, psls=()) -> dict:
     """Roofline of the neighbourhood kernel: 2 lane-ops per (neighbour, shift) term against the
     measured FP32-add / integer-add / logic-op mix rate, scaled to the clock of the timed region;
     also on live terms, and against the lookup ceiling of the kernel's own inner pattern."""
@@ -321,7 +334,7 @@ def hot_roofline(walks_x_N: int, L: int, hot_avg_ms: float, peak: dict, mhz_run:
     achieved = walks_x_N * 2 * tc["nominal"] / sec
     achieved_live = walks_x_N * 2 * tc["live"] / sec
     lookups = walks_x_N * tc["lookups"] / sec
-    out = {"bound": "alu", "kernel": "k_hot_batched", "achieved": achieved / 1e12, "peak": p_mix / 1e12,
+    out = {"bound": "alu", "kernel": kernel, "achieved": achieved / 1e12, "peak": p_mix / 1e12,
            "unit": "Tops/s", "frac": achieved / p_mix,
            "peak_basis": f"measured: psl_alu_peak mix microbenchmark (FP32 add, integer add, logic op 1:1:1 on "
                          f"{peak['sm_count']} SMs) {peak['mix'] / 1e12:.2f} Tops/s at {mhz_peak:.0f} MHz, scaled to "
@@ -334,6 +347,14 @@ def hot_roofline(walks_x_N: int, L: int, hot_avg_ms: float, peak: dict, mhz_run:
                               "flip_evals_per_s_ceiling": p_lookup / tc["lookups"],
                               "frac": lookups / p_lookup},
            "traffic": None, "issue_frac": None}
+    if kernel.startswith("k_hot_alpha2"):
+        # the closed form does no table lookups: its own ceiling is the bit-plane step rate
+        steps = plane_steps_per_flip_eval(L, psls)
+        p_popc = peak["popc"] * scale
+        out["lookup_ceiling"] = None
+        out["plane_step_ceiling"] = {"plane_steps_per_s_measured": peak["popc"], "plane_steps_per_flip_eval": steps,
+                                     "flip_evals_per_s_ceiling": p_popc / steps,
+                                     "frac": walks_x_N * steps / sec / p_popc}
     if counters:
         out["traffic"] = counters.get("bytes_per_launch")
         if counters.get("warp_inst_per_launch") and peak.get("sm_count"):
@@ -403,7 +424,8 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
 
     peak = measure_alu_peak(local, stream)
-    with P.Context(arena_tensor=arena, stream=stream, max_walks=len(specs), device=local) as ctx:
+    with P.Context(arena_tensor=arena, stream=stream, max_walks=len(specs), device=local,
+                   alpha2_tables=args.alpha2_tables) as ctx:
         # the first walks keep a per-step trace so that the FP32 score error can be stated
         n_traced = min(8, len(specs))
         ids = [ctx.submit_ex(s.L, s.seed, s.alpha1, s.alpha2, s.budget, topk=s.topk,
@@ -432,6 +454,8 @@ def run_ours(args):
         prof = ctx.profile_read()
         ctx.profile(0)
         ms = e0.elapsed_time(e1)
+        hot_name = ctx.hot_variant()
+        psls = [ctx.poll(i)["psl"] for i in ids[:64]]
         # the same steps as plain launches (no graph, no events), for comparison
         ctx.set_steps_per_graph(0)
         barrier()
@@ -456,7 +480,8 @@ def run_ours(args):
     n_hot, hot_ms = prof.get("hot", (0, 0.0))
     hot_avg_ms = hot_ms / max(n_hot, 1)
     mhz = clocks.get("sm_mhz") or peak["max_clock_mhz"]
-    roof = hot_roofline(len(specs) * N, L, hot_avg_ms, peak, mhz, stored_counters("k_hot_batched", wl.name))
+    roof = hot_roofline(len(specs) * N, L, hot_avg_ms, peak, mhz, stored_counters(hot_name, wl.name), hot_name,
+                        psls)
     roof["hot_launches_timed"] = n_hot
     kernels = {k: {"launches": n, "avg_ms": (ms_ / n if n else 0.0)} for k, (n, ms_) in breakdown.items() if n}
     # kernels per step: the neighbourhood score, then either one fused kernel (short walks) or
@@ -487,7 +512,7 @@ def run_ours(args):
         t0 = time.perf_counter()
         hot = dict(hot_threads=tuned[0], hot_tile_sb=tuned[1]) if tuned else {}
         with P.Context(arena_tensor=arena, stream=stream, max_walks=len(specs), device=local,
-                       steps_per_graph=G, **hot) as ctx:
+                       steps_per_graph=G, alpha2_tables=args.alpha2_tables, **hot) as ctx:
             ids = [ctx.submit(s.L, s.seed, s.alpha1, s.alpha2, s.budget) for s in specs]
             ctx.step(args.steps)
             psl_best, seqs = ctx.best_many(ids)      # every walk's best sequence, one synchronisation
@@ -546,6 +571,8 @@ def run_ours(args):
                 prof_o = oc.profile_read()
                 oc.profile(0)
                 ms_o = e0.elapsed_time(e1)
+                name_o = oc.hot_variant()
+                psls_o = [oc.poll(w)["psl"] for w in sorted(oc.L_of)[:64]]
                 quality = None
                 if specs_o[0].alpha1 == specs_o[0].alpha2 == 2:
                     # merit factor L^2 / (2 E) of every walk's lowest-energy pivot so far
@@ -556,13 +583,14 @@ def run_ours(args):
             Lo, No = specs_o[0].L, specs_o[0].N
             n_hot, hot_ms_o = prof_o.get("hot", (0, 0.0))
             roof_o = hot_roofline(len(specs_o) * No, Lo, hot_ms_o / max(n_hot, 1), peak, mhz,
-                                  stored_counters("k_hot_batched", wl_o.name))
+                                  stored_counters(name_o, wl_o.name), name_o, psls_o)
             others[wl_o.name] = {"value": len(specs_o) * No * k_o / (ms_o / 1000.0), "unit": UNIT,
                                  "ms_per_step": ms_o / k_o, "steps": k_o, "graph_steps": k_o,
-                                 "hot_kernel": {"threads": tune_o[0], "tile_superblocks": tune_o[1],
+                                 "hot_kernel": {"threads": tune_o[0], "tile_superblocks": tune_o[1], "name": name_o,
                                                 "avg_ms": hot_ms_o / max(n_hot, 1)},
                                  "roofline_frac": roof_o["frac"], "roofline_frac_live_terms": roof_o["frac_live_terms"],
-                                 "lookup_ceiling_frac": roof_o["lookup_ceiling"]["frac"],
+                                 "lookup_ceiling_frac": (roof_o["lookup_ceiling"] or {}).get("frac"),
+                                 "plane_step_ceiling_frac": (roof_o.get("plane_step_ceiling") or {}).get("frac"),
                                  "issue_frac": roof_o["issue_frac"], "traffic": roof_o["traffic"],
                                  "init_s": t_init, "description": wl_o.description}
             if quality:

@@ -90,6 +90,10 @@ typedef struct {
                                for the producer / consumer form (with hot_tile_sb 16 / 32); 0 = auto */
   int32_t max_sms;          /* SMs' worth of resident blocks the persistent kernels launch (0 = all);
                                lets contexts on different streams share the GPU side by side */
+  int32_t alpha2_tables;    /* 0: batches whose every walk has alpha1 = alpha2 = 2 and L <= 4095 (the
+                               merit-factor case) are scored by the closed form of Eq. 4 at alpha = 2
+                               (exact integer changes of F from bit planes of C); 1: by the subset-sum
+                               tables like every other batch.  Results are identical. */
 } psl_config;
 
 /* Per-walk parameters of psl_submit_ex.  n_lmt, flip_lmt <= 0 and ls_lmt < 0 take
@@ -237,7 +241,7 @@ PSL_API int psl_transfer_bytes(psl_ctx *ctx, uint64_t *h2d, uint64_t *d2h);
 PSL_API int psl_set_steps_per_graph(psl_ctx *ctx, int32_t steps);
 
 /* Measured issue rates of the CUDA-core pipes that bound the neighbourhood kernel (no
- * counterpart in the paper: the denominator of its roofline).  Four kernels fill every SM
+ * counterpart in the paper: the denominator of its roofline).  Five kernels fill every SM
  * of the device for a few tens of milliseconds each, timed with CUDA events on stream.
  * Rates are per second over the whole device, at whatever SM clock the device ran. */
 typedef struct {
@@ -250,7 +254,9 @@ typedef struct {
   double mix;               /* FP32 add, integer add and logic op 1:1:1, lane-ops per second */
   double lookup;            /* the neighbourhood kernel's inner pattern (shift, logic op forming a
                                table address, shared-memory load, FP32 add): lookups per second */
-  double ms[4];             /* duration of the timed launch of each (fadd, alu, mix, lookup) */
+  double popc;              /* the bit-plane step of the alpha = 2 closed form (three-input logic op,
+                               population count, integer add): plane steps per second        */
+  double ms[5];             /* duration of the timed launch of each (fadd, alu, mix, lookup, popc) */
 } psl_alu_peak_t;
 
 /* Runs the microbenchmarks on device (stream: a cudaStream_t of that device, or NULL) and
@@ -268,6 +274,12 @@ PSL_API int psl_alu_peak(int32_t device, void *stream, psl_alu_peak_t *out);
  * changes.  Returns threads | (tile_sb << 16) of the choice, PSL_ESTATE when no walk
  * is running, PSL_EINVAL for the plain form or reps < 1. */
 PSL_API int psl_autotune(psl_ctx *ctx, int reps);
+
+/* Writes into name (cap bytes, NUL-terminated, truncated if short) the name of the
+ * neighbourhood kernel the next step of ctx launches, after admitting queued walks: e.g.
+ * "k_hot_pc<28,32,8>", "k_hot_batched<512,16,4>", "k_hot_alpha2<256>", "k_hot_plain".
+ * Returns the length of the full name, PSL_EINVAL for a null argument or cap < 1. */
+PSL_API int psl_hot_variant(psl_ctx *ctx, char *name, int32_t cap);
 
 /* Sets the neighbourhood-kernel configuration of the batched form directly (for a
  * choice cached from an earlier psl_autotune).  PSL_EINVAL for unsupported values. */

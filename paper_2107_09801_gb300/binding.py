@@ -26,7 +26,7 @@ class psl_config(ct.Structure):
     _fields_ = [("n_lmt", ct.c_int32), ("ls_lmt", ct.c_int32), ("flip_lmt", ct.c_int32), ("device", ct.c_int32),
                 ("arena_bytes", ct.c_uint64), ("arena", ct.c_void_p), ("stream", ct.c_void_p), ("form", ct.c_int32),
                 ("max_walks", ct.c_int32), ("hot_tile_sb", ct.c_int32), ("steps_per_graph", ct.c_int32),
-                ("hot_threads", ct.c_int32), ("max_sms", ct.c_int32)]
+                ("hot_threads", ct.c_int32), ("max_sms", ct.c_int32), ("alpha2_tables", ct.c_int32)]
 
 
 class psl_walk_params(ct.Structure):
@@ -67,7 +67,7 @@ assert TRACE_DTYPE.itemsize == 128  # psl_trace_rec has no implicit padding
 class psl_alu_peak_t(ct.Structure):
     _fields_ = [("sm_count", ct.c_int32), ("max_clock_mhz", ct.c_int32), ("blocks_per_sm", ct.c_int32),
                 ("threads_per_block", ct.c_int32), ("fadd", ct.c_double), ("alu", ct.c_double), ("mix", ct.c_double),
-                ("lookup", ct.c_double), ("ms", ct.c_double * 4)]
+                ("lookup", ct.c_double), ("popc", ct.c_double), ("ms", ct.c_double * 5)]
 
 
 EXPORTED = ["psl_config_default", "psl_init", "psl_submit", "psl_submit_ex", "psl_step", "psl_poll", "psl_best",
@@ -75,7 +75,8 @@ EXPORTED = ["psl_config_default", "psl_init", "psl_submit", "psl_submit_ex", "ps
             "psl_last_error", "psl_profile", "psl_profile_read", "psl_autotune", "psl_set_hot_config",
             "psl_autocorr_static", "psl_inject_stall", "psl_set_max_sms",
             "psl_best_fitness", "psl_transfer_bytes", "psl_set_steps_per_graph", "psl_alu_peak",
-            "psl_shard_layout", "psl_shard_score", "psl_shard_select", "psl_shard_decide", "psl_best_many"]
+            "psl_shard_layout", "psl_shard_score", "psl_shard_select", "psl_shard_decide", "psl_best_many",
+            "psl_hot_variant"]
 
 _lib = None
 
@@ -112,6 +113,7 @@ def lib():
             "psl_profile_read": (ct.c_int, [P, ct.POINTER(psl_kernel_time), ct.c_size_t]),
             "psl_autotune": (ct.c_int, [P, ct.c_int]),
             "psl_set_hot_config": (ct.c_int, [P, ct.c_int32, ct.c_int32]),
+            "psl_hot_variant": (ct.c_int, [P, ct.c_char_p, ct.c_int32]),
             "psl_autocorr_static": (ct.c_int, [P, ct.c_uint32, P, P]),
             "psl_inject_stall": (ct.c_int, [P, ct.c_int64]),
             "psl_set_max_sms": (ct.c_int, [P, ct.c_int32]),
@@ -290,13 +292,15 @@ class Context:
 
     def __init__(self, *, form: str = "batched", arena_bytes: int = 0, arena_tensor=None, stream=None,
                  max_walks: int = 4096, n_lmt: int = 6912, ls_lmt: int = 2000, flip_lmt: int = 10, device: int = 0,
-                 hot_tile_sb: int = 0, steps_per_graph: int = 0, hot_threads: int = 0, max_sms: int = 0):
+                 hot_tile_sb: int = 0, steps_per_graph: int = 0, hot_threads: int = 0, max_sms: int = 0,
+                 alpha2_tables: bool = False):
         cfg = psl_config_default()
         cfg.n_lmt, cfg.ls_lmt, cfg.flip_lmt, cfg.device = n_lmt, ls_lmt, flip_lmt, device
         cfg.form = PSL_FORM_PLAIN if form == "plain" else PSL_FORM_BATCHED
         cfg.max_walks, cfg.hot_tile_sb, cfg.steps_per_graph = max_walks, hot_tile_sb, steps_per_graph
         cfg.hot_threads = hot_threads
         cfg.max_sms = max_sms
+        cfg.alpha2_tables = 1 if alpha2_tables else 0
         self._arena_tensor = arena_tensor
         if arena_tensor is not None:
             cfg.arena = arena_tensor.data_ptr()
@@ -383,6 +387,14 @@ class Context:
                 json.dump(table, f, indent=1, sort_keys=True)
             os.replace(tmp, cache)
         return t, sb
+
+    def hot_variant(self) -> str:
+        """Name of the neighbourhood kernel the next step launches (queued walks admitted)."""
+        buf = ct.create_string_buffer(64)
+        rc = lib().psl_hot_variant(self.h, buf, 64)
+        if rc < 0:
+            raise PslError(rc, "psl_hot_variant failed")
+        return buf.value.decode()
 
     def _set_hot(self, threads: int, tile_sb: int) -> None:
         psl_set_hot_config(self.h, threads, tile_sb)

@@ -10,8 +10,10 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libpsl.so")
-SOURCES = ["psl_kernels.cu", "psl_hot.cu", "psl_runtime.cu", "psl_static.cu", "psl_peak.cu"]
-HEADERS = [os.path.join(CSRC, "psl_internal.h"), os.path.join(CSRC, "psl_device.cuh"), os.path.join(ROOT, "include", "psl.h")]
+SOURCES = ["psl_kernels.cu", "psl_recheck.cu", "psl_tail.cu", "psl_hot.cu", "psl_alpha2.cu", "psl_runtime.cu",
+           "psl_static.cu", "psl_peak.cu"]
+HEADERS = [os.path.join(CSRC, "psl_internal.h"), os.path.join(CSRC, "psl_device.cuh"), os.path.join(CSRC, "psl_step.cuh"),
+           os.path.join(ROOT, "include", "psl.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O2,-fvisibility=hidden",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]

@@ -230,10 +230,12 @@ inline __device__ double wide_to_double(const uint32_t (&a)[kWideLimbs]) {
 // with s = 2^(-a*e).  Each is (ra - rb) * sum_i ra^i rb^(a-1-i), ra = |c+d|/2^e, rb = |c|/2^e:
 // a sum of non-negative terms, so the relative error stays below (2a+1) 2^-24 (plus an
 // absolute underflow term below 2^-140).
+// (c and c +- 2, c +- 4 are integers below 2^24, exact in FP32: one conversion serves all five.)
 __device__ __forceinline__ float4 tables_for(int c, uint32_t alpha, float inv2e) {
-  const float rb = fabsf((float)c) * inv2e;
-  const float r0 = fabsf((float)(c + 4)) * inv2e, r1 = fabsf((float)(c - 4)) * inv2e;
-  const float r2 = fabsf((float)(c + 2)) * inv2e, r3 = fabsf((float)(c - 2)) * inv2e;
+  const float fc = (float)c;
+  const float rb = fabsf(fc) * inv2e;
+  const float r0 = fabsf(fc + 4.f) * inv2e, r1 = fabsf(fc - 4.f) * inv2e;
+  const float r2 = fabsf(fc + 2.f) * inv2e, r3 = fabsf(fc - 2.f) * inv2e;
   float S0 = 1.f, S1 = 1.f, S2 = 1.f, S3 = 1.f, pb = 1.f;
   for (uint32_t n = 1; n < alpha; n++) {
     pb = pb * rb;
@@ -247,6 +249,22 @@ __device__ __forceinline__ float4 tables_for(int c, uint32_t alpha, float inv2e)
 
 __device__ __forceinline__ float absmax4(float4 t) {
   return fmaxf(fmaxf(fabsf(t.x), fabsf(t.y)), fmaxf(fabsf(t.z), fabsf(t.w)));
+}
+
+// Exact neighbour PSL over the near-peak list: max_k |C_k + delta_jk| for |C_k| >= PSL - 8.
+__device__ __forceinline__ int neighbour_psl(const WalkDev &W, const int2 *list, int n, int j, int L, int sj,
+                                             int floor_c, int cur) {
+  for (int q = 0; q < n; q++) {
+    const int2 e = list[q];
+    const int k = e.x, c = e.y;
+    if ((c < 0 ? -c : c) < floor_c) continue;
+    int part = 0;
+    if (j + k < L) part += sval(W.bits, j + k);
+    if (j >= k) part += sval(W.bits, j - k);
+    const int cn = c - 2 * sj * part;
+    cur = max(cur, cn < 0 ? -cn : cn);
+  }
+  return cur;
 }
 
 // Compensated flush of an FP32 block sum into (hi, lo): hi + lo keeps every flushed value.

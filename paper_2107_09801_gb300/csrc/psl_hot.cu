@@ -4,6 +4,7 @@
 // one-thread-per-neighbour kernel of the paper's execution model.
 #include <climits>
 #include <cstdint>
+#include <cstdio>
 
 #include "psl_device.cuh"
 #include "psl_internal.h"
@@ -215,22 +216,6 @@ __device__ __forceinline__ void group_generic(float &a0, float &a1, uint32_t bsw
       a1 += k <= kin ? r_in : (k <= kout ? r_ed : 0.f);
     }
   }
-}
-
-// Exact neighbour PSL over the near-peak list: max_k |C_k + delta_jk| for |C_k| >= PSL - 8.
-__device__ __forceinline__ int neighbour_psl(const WalkDev &W, const int2 *list, int n, int j, int L, int sj,
-                                             int floor_c, int cur) {
-  for (int q = 0; q < n; q++) {
-    const int2 e = list[q];
-    const int k = e.x, c = e.y;
-    if ((c < 0 ? -c : c) < floor_c) continue;
-    int part = 0;
-    if (j + k < L) part += sval(W.bits, j + k);
-    if (j >= k) part += sval(W.bits, j - k);
-    const int cn = c - 2 * sj * part;
-    cur = max(cur, cn < 0 ? -cn : cn);
-  }
-  return cur;
 }
 
 // One super-block where every lane has both partners for all 30 shifts; wu and wv point at
@@ -1125,6 +1110,13 @@ bool hot_config_supported(uint32_t threads, uint32_t tile_sb) {
 }
 
 uint32_t hot_flush_for(uint32_t maxL) { return maxL >= 4096u ? 8u : 4u; }
+
+int hot_batched_name(const LaunchCtx &c, char *out, int cap) {
+  const uint32_t fb = c.hot_flush_sb == 4 ? 4u : 8u;
+  if (is_pc(c.hot_threads))
+    return snprintf(out, (size_t)cap, "k_hot_pc<%u,%u,%u>", c.hot_threads / 32, pc_nsb(c.hot_threads, fb), fb);
+  return snprintf(out, (size_t)cap, "k_hot_batched<%u,%u,%u>", c.hot_threads, c.hot_tile_sb, fb);
+}
 
 cudaError_t prepare_hot_kernels() {
   {

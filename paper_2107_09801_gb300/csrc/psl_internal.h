@@ -127,6 +127,7 @@ struct LaunchCtx {
   uint32_t hot_tile_sb;    // super-blocks per k-tile
   uint32_t hot_flush_sb;   // super-blocks per block sum of the batched kernel (4 or 8)
   uint32_t sm_count;
+  uint32_t alpha2;         // every running walk has alpha = 2 and L <= kA2MaxL: the closed-form score
   uint32_t maxL;           // longest walk of an initialisation launch
   uint32_t ninit;          // walks of an initialisation launch
   cudaStream_t stream;
@@ -135,15 +136,27 @@ struct LaunchCtx {
 // ---- launchers (psl_kernels.cu) ----
 cudaError_t prepare_kernels();      // one-off kernel attributes (call before any capture)
 cudaError_t prepare_hot_kernels();  // the neighbourhood kernels' part of it (psl_hot.cu)
+cudaError_t prepare_recheck_kernel();  // psl_recheck.cu
+cudaError_t prepare_tail_kernel();     // psl_tail.cu
 cudaError_t launch_init_bits(const LaunchCtx &c);
 cudaError_t launch_autocorr(const LaunchCtx &c);
 cudaError_t launch_apply(const LaunchCtx &c);
 cudaError_t launch_hot_batched(const LaunchCtx &c);
+// neighbourhood score of a batch: the alpha = 2 closed form (psl_alpha2.cu) when c.alpha2,
+// else the subset-sum table kernels (psl_hot.cu)
+cudaError_t launch_hot(const LaunchCtx &c);
+cudaError_t launch_hot_alpha2(const LaunchCtx &c);
+cudaError_t prepare_alpha2_kernels();
+// name of the neighbourhood kernel that launch_hot runs for c (for profiles and reports),
+// snprintf-style: the length of the full name
+int hot_kernel_name(const LaunchCtx &c, char *out, int cap);
+int hot_batched_name(const LaunchCtx &c, char *out, int cap);
 cudaError_t launch_hot_plain(WalkDev *hdr_one, uint32_t N, cudaStream_t s);
 cudaError_t launch_select(const LaunchCtx &c);
 cudaError_t launch_recheck(const LaunchCtx &c);
 cudaError_t launch_decide(const LaunchCtx &c);
 cudaError_t launch_step_tail(const LaunchCtx &c);  // select..apply in one kernel, short walks only
+constexpr uint32_t kA2MaxL = 4095;  // walks up to this length can take the alpha = 2 closed form
 constexpr uint32_t kTailMaxL = kApplyChunk;      // walks up to this length (one update chunk, one re-check chunk)
 constexpr uint32_t kTailMaxN = 2048;             // and windows up to this size (one warp selects)
 cudaError_t launch_start_init(const LaunchCtx &c);

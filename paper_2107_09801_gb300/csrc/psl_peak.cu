@@ -9,6 +9,8 @@
 //   mix     FP32 add, integer add and logic op, one of each   (lane-ops per second)
 //   lookup  the neighbourhood kernel's inner pattern: a shift, a logic op forming a table
 //           address, a shared-memory load and an FP32 add    (lookups per second)
+//   popc    the bit-plane step of the alpha = 2 closed form: a logic op, a population count
+//           and an integer add                                (plane steps per second)
 // Each op is written as inline PTX on a dependency chain the compiler cannot fold (adds
 // and logic ops alternate; FP32 adds do not reassociate), and every chain ends in a value
 // that is stored conditionally, so no work is removed.
@@ -135,6 +137,29 @@ __global__ void __launch_bounds__(kPeakThreads) k_peak_lookup(float *sink, int i
   if (s == -1.2345f) sink[0] = s;
 }
 
+// 4 x kChains bit-plane steps per iteration, each: a three-input logic op (an AND of the
+// running value with two words), a population count, and an integer add into the running value
+__global__ void __launch_bounds__(kPeakThreads) k_peak_popc(uint32_t *sink, int iters, uint32_t y) {
+  uint32_t x[kChains], w[kChains];
+#pragma unroll
+  for (int i = 0; i < kChains; i++) x[i] = threadIdx.x * 0x9E3779B9u + (uint32_t)i, w[i] = ~(y * (uint32_t)(i + 3));
+  for (int it = 0; it < iters; it++) {
+#pragma unroll
+    for (int u = 0; u < 4; u++)
+#pragma unroll
+      for (int i = 0; i < kChains; i++) {
+        uint32_t a, c;
+        asm volatile("lop3.b32 %0, %1, %2, %3, 0x80;" : "=r"(a) : "r"(x[i]), "r"(w[i]), "r"(y));  // x & w & y
+        asm volatile("popc.b32 %0, %1;" : "=r"(c) : "r"(a));
+        x[i] = iadd_ptx(x[i], c);
+      }
+  }
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kChains; i++) s ^= x[i];
+  if (s == 0x12345u) sink[0] = s;
+}
+
 }  // namespace
 
 extern "C" int psl_alu_peak(int32_t device, void *stream, psl_alu_peak_t *out) {
@@ -157,10 +182,10 @@ extern "C" int psl_alu_peak(int32_t device, void *stream, psl_alu_peak_t *out) {
     rc = PSL_ECUDA;
   } else {
     // iterations sized for launches of a few tens of milliseconds
-    const int it_fadd = 40000, it_alu = 20000, it_mix = 15000, it_lookup = 15000;
-    const double ops[4] = {threads * it_fadd * 4 * kChains, threads * it_alu * 4 * kChains,
-                           threads * it_mix * 6 * kChains, threads * it_lookup * 24};
-    for (int kind = 0; kind < 4 && rc == PSL_OK; kind++) {
+    const int it_fadd = 40000, it_alu = 20000, it_mix = 15000, it_lookup = 15000, it_popc = 10000;
+    const double ops[5] = {threads * it_fadd * 4 * kChains, threads * it_alu * 4 * kChains,
+                           threads * it_mix * 6 * kChains, threads * it_lookup * 24, threads * it_popc * 4 * kChains};
+    for (int kind = 0; kind < 5 && rc == PSL_OK; kind++) {
       float ms = 0.f;
       for (int rep = 0; rep < 2 && rc == PSL_OK; rep++) {  // the first launch warms up
         if (rep == 1 && cudaEventRecord(e0, s) != cudaSuccess) rc = PSL_ECUDA;
@@ -169,7 +194,8 @@ extern "C" int psl_alu_peak(int32_t device, void *stream, psl_alu_peak_t *out) {
           case 1: k_peak_alu<<<blocks, kPeakThreads, 0, s>>>((uint32_t *)sink, it_alu, 0x9E3779B9u, 0x7F4A7C15u); break;
           case 2: k_peak_mix<<<blocks, kPeakThreads, 0, s>>>((uint32_t *)sink, it_mix, 0x9E3779B9u, 0x7F4A7C15u, 1e-7f);
             break;
-          default: k_peak_lookup<<<blocks, kPeakThreads, 0, s>>>((float *)sink, it_lookup, 0x2545F491u); break;
+          case 3: k_peak_lookup<<<blocks, kPeakThreads, 0, s>>>((float *)sink, it_lookup, 0x2545F491u); break;
+          default: k_peak_popc<<<blocks, kPeakThreads, 0, s>>>((uint32_t *)sink, it_popc, 0xF0F0F0F7u); break;
         }
         if (cudaGetLastError() != cudaSuccess) rc = PSL_ECUDA;
       }
@@ -183,6 +209,7 @@ extern "C" int psl_alu_peak(int32_t device, void *stream, psl_alu_peak_t *out) {
         if (kind == 1) out->alu = rate;
         if (kind == 2) out->mix = rate;
         if (kind == 3) out->lookup = rate;
+        if (kind == 4) out->popc = rate;
       }
     }
   }

@@ -150,6 +150,7 @@ struct psl_ctx {
   int64_t next_id = 0;
   uint32_t hot_flush_sb = 8;  // super-blocks per block sum of the neighbourhood kernel
   bool tail_fused = false;    // every running walk is short: select..apply run as one kernel
+  bool alpha2 = false;        // every running walk has alpha1 = alpha2 = 2, L <= kA2MaxL: closed-form score
   uint32_t sm_count = 152;   // SMs the persistent kernels are sized for
   uint32_t dev_sms = 152;    // SMs of the device
   std::string err;
@@ -592,6 +593,17 @@ static int rebuild_active(psl_ctx *ctx) {
     ctx->tail_fused = short_only;
     drop_graph(ctx);  // captured with the other kernel sequence
   }
+  // alpha = 2 batches of short walks take the closed-form score (unless the configuration
+  // asks for the tables); it scores every neighbour whole, so their k range is never split
+  bool a2 = !ctx->active.empty() && ctx->cfg.alpha2_tables == 0 && ctx->cfg.form == PSL_FORM_BATCHED;
+  for (uint32_t s : ctx->active) {
+    const WalkDev &h = ctx->h_hdr[s];
+    a2 = a2 && h.alpha1 == 2 && h.alpha2 == 2 && h.L <= kA2MaxL && h.shard_count <= 1;
+  }
+  if (a2 != ctx->alpha2) {
+    ctx->alpha2 = a2;
+    drop_graph(ctx);  // captured with the other kernel
+  }
   // Split every walk's k range into chunks when the neighbour blocks alone would leave
   // SMs idle (few walks, or a long walk on its own): aim for about four blocks per SM.
   const uint32_t T_ = (uint32_t)ctx->cfg.hot_threads;
@@ -599,7 +611,7 @@ static int rebuild_active(psl_ctx *ctx) {
   for (uint32_t s : ctx->active) nblocks += (ctx->h_hdr[s].N + T_ - 1) / T_;
   const uint64_t target = 4ull * (uint64_t)ctx->sm_count;
   uint32_t want = nblocks == 0 ? 1u : (uint32_t)std::min<uint64_t>(kKsplitMax, (target + nblocks - 1) / nblocks);
-  if (ctx->cfg.form == PSL_FORM_PLAIN) want = 1;  // the plain kernel scores each neighbour whole
+  if (ctx->cfg.form == PSL_FORM_PLAIN || a2) want = 1;  // these kernels score each neighbour whole
   for (uint32_t s : ctx->active) {
     WalkDev &h = ctx->h_hdr[s];
     const uint32_t unitK = kKchunkSbUnit * kSbK;
@@ -656,6 +668,7 @@ static LaunchCtx launch_ctx(psl_ctx *ctx, const uint32_t *d_list, Schedule *d_sc
   c.hot_threads = (uint32_t)ctx->cfg.hot_threads;
   c.hot_tile_sb = (uint32_t)ctx->cfg.hot_tile_sb;
   c.hot_flush_sb = ctx->hot_flush_sb;
+  c.alpha2 = ctx->alpha2 ? 1u : 0u;
   c.sm_count = ctx->sm_count;
   c.stream = ctx->stream;
   return c;
@@ -762,8 +775,7 @@ static int refresh_headers(psl_ctx *ctx) {
 // One step of the batched form.  Outside a capture each kernel may be bracketed by events
 // on the stream; inside a capture (captured = true) by event-record nodes of the graph.
 static cudaError_t enqueue_batched_step(psl_ctx *ctx, const LaunchCtx &c, bool captured) {
-  cudaError_t (*fns[5])(const LaunchCtx &) = {launch_hot_batched, launch_select, launch_recheck, launch_decide,
-                                               launch_apply};
+  cudaError_t (*fns[5])(const LaunchCtx &) = {launch_hot, launch_select, launch_recheck, launch_decide, launch_apply};
   int kinds[5] = {kPHot, kPSelect, kPRecheck, kPDecide, kPApply};
   int n = 5;
   if (ctx->tail_fused) {  // short walks only: selection, re-check, decision and update in one kernel
@@ -1285,11 +1297,11 @@ extern "C" int psl_autotune(psl_ctx *ctx, int reps) {
       if ((rc = rebuild_active(ctx))) return rc;
       LaunchCtx c = launch_ctx(ctx, ctx->d_active, ctx->d_sched);
       uint32_t *next = &ctx->d_sched->hot_next;
-      CK(launch_hot_batched(c));  // warm-up
+      CK(launch_hot(c));  // warm-up
       CK(cudaMemsetAsync(next, 0, 4, ctx->stream));
       CK(cudaEventRecord(a, ctx->stream));
       for (int r = 0; r < reps; r++) {
-        CK(launch_hot_batched(c));
+        CK(launch_hot(c));
         CK(cudaMemsetAsync(next, 0, 4, ctx->stream));  // the persistent kernel consumed its work counter
       }
       CK(cudaEventRecord(b, ctx->stream));
@@ -1306,6 +1318,15 @@ extern "C" int psl_autotune(psl_ctx *ctx, int reps) {
   drop_graph(ctx);  // captured with another kernel variant
   if ((rc = rebuild_active(ctx))) return rc;
   return best_t | (best_sb << 16);
+}
+
+extern "C" int psl_hot_variant(psl_ctx *ctx, char *name, int32_t cap) {
+  if (!ctx || !name || cap < 1) return PSL_EINVAL;
+  int rc = admit(ctx);
+  if (rc) return rc;
+  if (ctx->active_dirty && (rc = rebuild_active(ctx))) return rc;
+  if (ctx->cfg.form == PSL_FORM_PLAIN) return snprintf(name, (size_t)cap, "k_hot_plain");
+  return hot_kernel_name(launch_ctx(ctx, ctx->d_active, ctx->d_sched), name, cap);
 }
 
 extern "C" int psl_set_hot_config(psl_ctx *ctx, int32_t threads, int32_t tile_sb) {

@@ -1,0 +1,61 @@
+// psl_tail.cu -- the step after the neighbourhood score for batches of short walks
+// (arXiv 2107.09801, Algorithm 1): one block per walk runs selection, exact re-check,
+// decision and update back to back.  Its own translation unit, compiled in parallel.
+#include <cstdint>
+
+#include "psl_device.cuh"
+#include "psl_internal.h"
+#include "psl_step.cuh"
+
+namespace psl {
+
+// ------------------------------------------------------------------------------------
+// the step after the neighbourhood score for batches of short walks (every walk with one
+// update chunk, one re-check chunk and a window selected by one warp): one block per walk
+// runs selection, exact re-check, decision and update back to back, instead of four
+// launches of latency-bound kernels
+// ------------------------------------------------------------------------------------
+// Blocks of two warps: each walk's chain of phases is bound by latency, so the more walks
+// an SM holds at once the better (64 threads: 12 blocks per SM, against 3 of 256 threads;
+// measured at L = 1023 x 4096: 0.108 against 0.230 ms per step).
+constexpr int kTailThreads = 64;
+
+__global__ void __launch_bounds__(256, 3) k_step_tail(WalkDev *hdr, const uint32_t *active, Schedule *sched) {
+  // the neighbourhood kernel of this step has finished: rearm its work counter
+  if (blockIdx.x == 0 && threadIdx.x == 0) sched->hot_next = 0;
+  for (uint32_t a = blockIdx.x; a < sched->nactive; a += gridDim.x) {
+    WalkDev &W = hdr[active[a]];
+    __syncthreads();  // the previous walk's shared buffers are free
+    if (W.status != kRunning) continue;  // one reading for the block: nothing below changes it before it is read
+    if (threadIdx.x < 32) select_warp(W);
+    __syncthreads();  // candidates, bound and window PSL are visible to the block
+    const uint32_t nslots = min(W.ncand, (uint32_t)kQcap);
+    for (uint32_t qslot = 0; qslot < nslots; qslot++) {
+      __syncthreads();
+      recheck_one<true, kRcBoth>(W, 0, qslot);
+    }
+    __syncthreads();  // re-check partials are visible
+    decide_one(W);
+    __syncthreads();  // the decision (mode, k*, flips, next exponent) is visible
+    if (W.mode == kModeMove)
+      apply_move_dispatch(W, 0);
+    else
+      apply_one(W, 0);
+  }
+}
+
+static uint32_t g_tail_per_sm = 4;
+
+cudaError_t prepare_tail_kernel() {
+  int nb = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_step_tail, kTailThreads, 0);
+  g_tail_per_sm = (uint32_t)(nb > 0 ? nb : 1);
+  return e;
+}
+
+cudaError_t launch_step_tail(const LaunchCtx &c) {
+  k_step_tail<<<g_tail_per_sm * c.sm_count, kTailThreads, 0, c.stream>>>(c.hdr, c.active, c.sched);
+  return cudaGetLastError();
+}
+
+}  // namespace psl

@@ -550,12 +550,15 @@ def test_lowest_fitness_pivot_matches_oracle(P, form):
             ctx.best_fitness(oid)
 
 
-def test_merit_factor_workload_sampled_walks(P):
-    """The alpha = 2 workload at full size (L=1023, full neighbourhood, 4096 walks): every
-    walk's lowest energy equals sum C_k^2 of its sequence, and sampled walks follow the oracle."""
+@pytest.mark.parametrize("tables", [False, True])
+def test_merit_factor_workload_sampled_walks(P, tables):
+    """The alpha = 2 workload at full size (L=1023, full neighbourhood, 4096 walks), by the
+    closed form and by the tables: every walk's lowest energy equals sum C_k^2 of its
+    sequence, and sampled walks follow the oracle."""
     specs = W.labs_1023(4096, budget=12).walks
-    with P.Context(arena_bytes=ARENA, max_walks=len(specs), steps_per_graph=4) as ctx:
+    with P.Context(arena_bytes=ARENA, max_walks=len(specs), steps_per_graph=4, alpha2_tables=tables) as ctx:
         ids = [submit_spec(ctx, s, trace=False) for s in specs]
+        assert ctx.hot_variant().startswith("k_hot_batched" if tables else "k_hot_alpha2")
         ctx.run()
         got = [ctx.best_fitness(i) for i in ids]
         for E, seq in got[::97]:
@@ -565,6 +568,79 @@ def test_merit_factor_workload_sampled_walks(P):
             w = oracle_walk(specs[r])
             w.run(specs[r].budget)
             assert got[r][0] == w.F_best and np.array_equal(got[r][1], w.fbest_seq), r
+
+
+# ------------------------------------------------------------------------------------------------
+# alpha = 2: the closed-form score (bit planes of C) against the oracle, in every block size,
+# and the subset-sum tables on the same walks
+# ------------------------------------------------------------------------------------------------
+def alpha2_specs():
+    # lengths around the word boundaries of the planes, windows shorter than L, the largest
+    # length the closed form takes; phase switches every few steps
+    shapes = [(2, 2, 3), (3, 3, 4), (13, 13, 10), (33, 33, 12), (64, 64, 12), (100, 50, 15), (1023, 1023, 20),
+              (2047, 700, 12), (4095, 4095, 8)]
+    return [W.WalkSpec(L=L, seed=300 + r, alpha1=2, alpha2=2, n_lmt=n, ls_lmt=3, flip_lmt=3, budget=b)
+            for r, (L, n, b) in enumerate(shapes)]
+
+
+_ALPHA2_ORACLE = {}
+
+
+def alpha2_oracle(q, spec):
+    """The oracle's walk of alpha2_specs()[q] after its budget (run once per module)."""
+    if q not in _ALPHA2_ORACLE:
+        w = oracle_walk(spec)
+        _ALPHA2_ORACLE[q] = (w, w.run(spec.budget))
+    return _ALPHA2_ORACLE[q]
+
+
+@pytest.mark.parametrize("threads", [128, 256, 448, 512, 896])
+def test_alpha2_closed_form_matches_oracle(P, threads):
+    specs = alpha2_specs()
+    tile = 16 if threads == 448 else 32
+    with P.Context(arena_bytes=ARENA, max_walks=16, hot_threads=threads, hot_tile_sb=tile) as ctx:
+        ids = [submit_spec(ctx, s) for s in specs]
+        assert ctx.hot_variant() == f"k_hot_alpha2<{threads}>"
+        ctx.run()
+        for q, (i, s) in enumerate(zip(ids, specs)):
+            w, otr = alpha2_oracle(q, s)
+            compare_traces(ctx.trace(i, s.budget), otr, f"alpha2 {threads} L={s.L}")
+            compare_final_state(ctx.export_state(i), w, f"alpha2 {threads} L={s.L}")
+
+
+def test_alpha2_closed_form_extremes(P):
+    """Starts with the widest planes (all ones: |C_k| = L - k, 13 planes at L = 4095) and the
+    narrowest (a Barker sequence, |C_k| <= 1); the tables give the same trajectories."""
+    barker = np.array([1, 1, 1, 1, 1, -1, -1, 1, 1, -1, 1, -1, 1], dtype=np.int8)
+    specs = [W.WalkSpec(L=4095, seed=1, alpha1=2, alpha2=2, n_lmt=4095, ls_lmt=2, flip_lmt=4, budget=6),
+             W.WalkSpec(L=2000, seed=2, alpha1=2, alpha2=2, n_lmt=300, ls_lmt=2, flip_lmt=4, budget=6),
+             W.WalkSpec(L=13, seed=3, alpha1=2, alpha2=2, n_lmt=13, ls_lmt=2, flip_lmt=2, budget=8)]
+    inits = [np.ones(4095, dtype=np.int8), np.ones(2000, dtype=np.int8), barker]
+    res = {}
+    for tables in (False, True):
+        with P.Context(arena_bytes=ARENA, max_walks=8, alpha2_tables=tables) as ctx:
+            ids = [submit_spec(ctx, s, init_seq=q) for s, q in zip(specs, inits)]
+            name = ctx.hot_variant()
+            assert name.startswith("k_hot_batched") if tables else name.startswith("k_hot_alpha2"), name
+            ctx.run()
+            res[tables] = [ctx.trace(i, s.budget) for i, s in zip(ids, specs)]
+    for q, (s, s0) in enumerate(zip(specs, inits)):
+        otr = oracle_walk(s, s0=s0).run(s.budget)
+        compare_traces(res[False][q], otr, f"closed form L={s.L}")
+        compare_traces(res[True][q], otr, f"tables L={s.L}")
+
+
+def test_alpha2_mixed_batch_uses_tables(P):
+    """A batch with any walk outside the closed form's reach (alpha != 2, or L > 4095) is scored
+    by the tables throughout, with the same results."""
+    specs = alpha2_specs()[4:7] + [W.WalkSpec(L=255, seed=9, alpha1=2, alpha2=5, budget=10),
+                                   W.WalkSpec(L=5000, seed=10, alpha1=2, alpha2=2, budget=6)]
+    with P.Context(arena_bytes=ARENA, max_walks=16) as ctx:
+        ids = [submit_spec(ctx, s) for s in specs]
+        assert not ctx.hot_variant().startswith("k_hot_alpha2")
+        ctx.run()
+        for i, s in zip(ids, specs):
+            compare_traces(ctx.trace(i, s.budget), oracle_walk(s).run(s.budget), f"mixed L={s.L}")
 
 
 # ------------------------------------------------------------------------------------------------
@@ -612,10 +688,10 @@ def test_alu_peak_microbenchmark(P):
     from paper_2107_09801_gb300 import binding as B
     pk = B.psl_alu_peak(0, torch.cuda.current_stream().cuda_stream)
     assert pk["sm_count"] == torch.cuda.get_device_properties(0).multi_processor_count
-    per_clk = {k: pk[k] / (pk["sm_count"] * pk["max_clock_mhz"] * 1e6) for k in ("fadd", "alu", "mix", "lookup")}
+    per_clk = {k: pk[k] / (pk["sm_count"] * pk["max_clock_mhz"] * 1e6) for k in ("fadd", "alu", "mix", "lookup", "popc")}
     # lane-ops per SM per clock at the top clock: no pipe can exceed 4 schedulers x 32 lanes
     assert all(0 < v <= 128 * 1.02 for v in per_clk.values()), per_clk
-    assert per_clk["fadd"] > 32 and per_clk["mix"] > 32 and per_clk["lookup"] > 4, per_clk
+    assert per_clk["fadd"] > 32 and per_clk["mix"] > 32 and per_clk["lookup"] > 4 and per_clk["popc"] > 4, per_clk
     print("lane-ops (lookups) per SM per clock:", per_clk)
 
 
