@@ -32,15 +32,30 @@ namespace psl {
 namespace {
 
 constexpr int kA2Words = (int)((kA2MaxL - 1 + 31) / 32);  // words of shifts k = 1 .. L-1
+// two's-complement planes of |C_k| <= PSL <= L - 1 < 2^12 for L <= 4095: P = bitlen(PSL) + 1 <= 13
+constexpr int kA2MaxPlanes = 13;
+static_assert(kA2Words % 4 == 0 && kA2MaxL < 4096u, "plane groups of four words; 13 planes suffice");
 
-// Bit planes of C_k, k = 1 + 32 w + t in bit t of word w: 16 per word (four 16-byte vectors,
-// planes at and above P are zero), prefix sums of C within each word and over words.
+// Bit planes of C_k, k = 1 + 32 w + t in bit t of word w, plane-major so that four
+// consecutive words of one plane load as one 16-byte vector; prefix sums of C within each
+// word and over words.  (Plane words past the walk's last shift may hold an earlier walk's
+// values: they are only ever combined with windows that read 0 there.)
+// The sequence's bits forward (bit t of word m: x_{32m+t}) and reversed (r_i = x_{L-1-i}),
+// with zero words past the end: a position's partner windows are consecutive 32-bit
+// stretches of one of them (forward partners of j start at j + 1 in x, backward partners at
+// L - j in r), one shared load and one funnel shift per word, reading 0 past either end.
+constexpr int kA2BitWords = 2 * kA2Words + 8;
+constexpr int kA2PeakCap = 512;  // near-peak entries staged per item (more: read from the walk's list)
 struct A2Smem {
-  uint4 plane[kA2Words][4];
+  uint4 plane[kA2MaxPlanes][kA2Words / 4];
   int pre[kA2MaxL];      // pre[k]: sum of C over the shifts of k's word up to k
   int woff[kA2Words];    // sum of C over the words before w
+  uint32_t xs[kA2BitWords];
+  uint32_t rs[kA2BitWords];
+  int2 peak[kA2PeakCap];  // the near-peak entries (k, C_k) with |C_k| >= PSL - 8
   uint32_t next;
   int run;
+  int npeak;
 };
 
 __device__ __forceinline__ int a2_bitlen(uint32_t v) { return v ? 32 - __clz(v) : 0; }
@@ -50,57 +65,114 @@ __device__ __forceinline__ int a2_prefix(const A2Smem &sm, int K) {
   return K <= 0 ? 0 : sm.pre[K] + sm.woff[(K - 1) >> 5];
 }
 
-// sum over the words of one side of sum_p w_p popcount(plane_p[w] AND window_w): the window of
-// word w is win[base + dir 32 w] (bit t: x_{j + dir (1 + 32 w + t)}).
-template <int PQ>
-__device__ __forceinline__ int a2_side(const A2Smem &sm, const uint32_t *__restrict__ win, int base, int dir, int nw,
-                                       const int (&wt)[4 * PQ]) {
-  int cnt[4 * PQ];
+// full adder over bit slices: s = a + b + c mod 2, returns the carry
+__device__ __forceinline__ uint32_t a2_fa(uint32_t &s, uint32_t a, uint32_t b, uint32_t c) {
+  s = a ^ b ^ c;
+  return (a & b) | (c & (a ^ b));
+}
+
+// One side (forward or backward partners) of sum_p w_p popcount(plane_p[w] AND window_w) over
+// the words w < nw: window w is bits [start + 32 w, start + 32 w + 32) of the bit array arr
+// (bit t: x_{j +- (1 + 32 w + t)}); past the side's last shift it reads the zero words.
+// Words are taken four at a time through carry-save adders per plane (ones, twos, and a
+// popcount of the fours), so a population count serves four words instead of one: that unit
+// issues at an eighth of the logic-op rate.  Planes PLO .. PHI-1 of P (wider sequences of
+// planes go in two passes, to bound the registers of the counters).
+template <int PLO, int PHI, int P>
+__device__ __forceinline__ int a2_side(const A2Smem &sm, const uint32_t *arr, int start, int nw) {
+  constexpr int NP = PHI - PLO;
+  uint32_t ones[NP], twos[NP];
+  int fours[NP];
 #pragma unroll
-  for (int p = 0; p < 4 * PQ; p++) cnt[p] = 0;
-  for (int w = 0; w < nw; w++) {
-    const uint32_t x = __ldg(win + base + dir * 32 * w);
+  for (int p = 0; p < NP; p++) ones[p] = twos[p] = 0u, fours[p] = 0;
+  const int ng = (nw + 3) >> 2;
+  const int q0 = start >> 5, sh = start & 31;
+  uint32_t lo = arr[q0];
+  for (int g = 0; g < ng; g++) {
+    uint32_t x[4];
 #pragma unroll
-    for (int q = 0; q < PQ; q++) {
-      const uint4 pl = sm.plane[w][q];
-      cnt[4 * q + 0] += __popc(pl.x & x);
-      cnt[4 * q + 1] += __popc(pl.y & x);
-      cnt[4 * q + 2] += __popc(pl.z & x);
-      cnt[4 * q + 3] += __popc(pl.w & x);
+    for (int u = 0; u < 4; u++) {
+      const uint32_t hi = arr[q0 + 4 * g + u + 1];
+      x[u] = __funnelshift_r(lo, hi, sh);
+      lo = hi;
+    }
+#pragma unroll
+    for (int p = 0; p < NP; p++) {
+      const uint4 pl = sm.plane[PLO + p][g];
+      uint32_t s1, s2, s4;
+      const uint32_t c1 = a2_fa(s1, ones[p], pl.x & x[0], pl.y & x[1]);
+      const uint32_t c2 = a2_fa(s2, s1, pl.z & x[2], pl.w & x[3]);
+      ones[p] = s2;
+      const uint32_t c4 = a2_fa(s4, twos[p], c1, c2);
+      twos[p] = s4;
+      fours[p] += __popc(c4);
     }
   }
   int s = 0;
 #pragma unroll
-  for (int p = 0; p < 4 * PQ; p++) s += wt[p] * cnt[p];
+  for (int p = 0; p < NP; p++) {
+    const int v = __popc(ones[p]) + 2 * __popc(twos[p]) + 4 * fours[p];
+    const int q = PLO + p;
+    s += (q == P - 1 ? -(1 << q) : (1 << q)) * v;  // two's complement: the top plane weighs -2^(P-1)
+  }
   return s;
 }
 
+template <int P>
+__device__ __forceinline__ int a2_side_all(const A2Smem &sm, const uint32_t *arr, int start, int nw) {
+  if constexpr (P <= 8)
+    return a2_side<0, P, P>(sm, arr, start, nw);
+  else
+    return a2_side<0, 8, P>(sm, arr, start, nw) + a2_side<8, P, P>(sm, arr, start, nw);
+}
+
 // Exact Delta F of flipping position j (in the sequence) of walk W, alpha = 2.
-template <int PQ>
-__device__ __forceinline__ int a2_delta(const A2Smem &sm, const WalkDev &W, int j, int L, int P) {
-  int wt[4 * PQ];
-#pragma unroll
-  for (int p = 0; p < 4 * PQ; p++) wt[p] = p < P - 1 ? (1 << p) : (p == P - 1 ? -(1 << p) : 0);
+template <int P>
+__device__ __forceinline__ int a2_delta(const A2Smem &sm, const WalkDev &W, int j, int L) {
   const int kplus = L - 1 - j, kin = min(j, kplus);
-  // forward: words w < ceil(kplus / 32), windows at j + 1 + 32 w <= L - 1; backward: words
-  // w < ceil(j / 32), windows at j - 1 - 32 w >= 0.  Bits past either end read 0.
-  const int sx = a2_side<PQ>(sm, W.win_f, j + 1, 1, (kplus + 31) >> 5, wt);
-  const int sy = a2_side<PQ>(sm, W.win_r, j - 1, -1, (j + 31) >> 5, wt);
+  // forward partners x_{j+k}: x from j + 1, words w < ceil(kplus / 32); backward partners
+  // x_{j-k} = r_{L-j-1+k}: r from L - j, words w < ceil(j / 32)
+  const int sx = a2_side_all<P>(sm, sm.xs, j + 1, (kplus + 31) >> 5);
+  const int sy = a2_side_all<P>(sm, sm.rs, L - j, (j + 31) >> 5);
   int zd = 0;
-  for (int w = 0; w < ((kin + 31) >> 5); w++) {
-    const uint32_t d = __ldg(W.win_f + j + 1 + 32 * w) ^ __ldg(W.win_r + j - 1 - 32 * w);
-    const int lim = kin - 32 * w;  // shifts 1 + 32 w + t <= kin
-    zd += __popc(lim >= 32 ? d : d & ((1u << lim) - 1u));
+  {
+    const int qf = (j + 1) >> 5, sf = (j + 1) & 31, qr = (L - j) >> 5, sr = (L - j) & 31;
+    uint32_t fl = sm.xs[qf], rl = sm.rs[qr];
+    for (int w = 0; w < ((kin + 31) >> 5); w++) {
+      const uint32_t fh = sm.xs[qf + w + 1], rh = sm.rs[qr + w + 1];
+      const uint32_t d = __funnelshift_r(fl, fh, sf) ^ __funnelshift_r(rl, rh, sr);
+      fl = fh, rl = rh;
+      const int lim = kin - 32 * w;  // shifts 1 + 32 w + t <= kin
+      zd += __popc(lim >= 32 ? d : d & ((1u << lim) - 1u));
+    }
   }
   const int X = a2_prefix(sm, kplus) - 2 * sx;
   const int Y = a2_prefix(sm, j) - 2 * sy;
   const int Z = kin - 2 * zd;
-  const int sj = getbit(W.bits, j) ? -1 : 1;
+  const int sj = ((sm.xs[j >> 5] >> (j & 31)) & 1u) ? -1 : 1;
   return -4 * sj * (X + Y) + 4 * (L - 1) + 8 * Z;
 }
 
+__device__ __forceinline__ int a2_delta_any(const A2Smem &sm, const WalkDev &W, int j, int L, int P) {
+  switch (P) {
+    case 1: return a2_delta<1>(sm, W, j, L);
+    case 2: return a2_delta<2>(sm, W, j, L);
+    case 3: return a2_delta<3>(sm, W, j, L);
+    case 4: return a2_delta<4>(sm, W, j, L);
+    case 5: return a2_delta<5>(sm, W, j, L);
+    case 6: return a2_delta<6>(sm, W, j, L);
+    case 7: return a2_delta<7>(sm, W, j, L);
+    case 8: return a2_delta<8>(sm, W, j, L);
+    case 9: return a2_delta<9>(sm, W, j, L);
+    case 10: return a2_delta<10>(sm, W, j, L);
+    case 11: return a2_delta<11>(sm, W, j, L);
+    case 12: return a2_delta<12>(sm, W, j, L);
+    default: return a2_delta<13>(sm, W, j, L);
+  }
+}
+
 template <int NT>
-__global__ void __launch_bounds__(NT) k_hot_alpha2(WalkDev *hdr, const HotItem *items, Schedule *sched) {
+__global__ void __launch_bounds__(NT, 1024 / NT) k_hot_alpha2(WalkDev *hdr, const HotItem *items, Schedule *sched) {
   constexpr int NW = NT / 32;
   __shared__ A2Smem sm;
   const int lane = (int)(threadIdx.x & 31u), warp = (int)(threadIdx.x >> 5);
@@ -110,6 +182,7 @@ __global__ void __launch_bounds__(NT) k_hot_alpha2(WalkDev *hdr, const HotItem *
       const uint32_t nx = atomicAdd(&sched->hot_next, 1u);
       sm.next = nx;
       sm.run = nx < sched->nitems && hdr[items[nx].slot].status == kRunning;  // one reading for the block
+      sm.npeak = 0;
     }
     __syncthreads();
     const uint32_t item = sm.next;
@@ -120,17 +193,41 @@ __global__ void __launch_bounds__(NT) k_hot_alpha2(WalkDev *hdr, const HotItem *
     const int L = (int)W.L, N = (int)W.N;
     const int P = a2_bitlen((uint32_t)W.psl) + 1;  // |C_k| <= PSL < 2^(P-1) for k >= 1
     const int nw = (L - 1 + 31) >> 5;
+    // the bits forward and reversed, zero past the end of the sequence
+    const int nb = (L + 31) >> 5;
+    for (int m = (int)threadIdx.x; m < kA2BitWords; m += NT) {
+      sm.xs[m] = m < nb ? W.bits[m] : 0u;  // the packed sequence keeps its padding bits 0
+      // r word m, bit t: x_{L-1-32m-t} = bit 31-t of the 32 bits from L-32-32m
+      sm.rs[m] = m < nb ? __brev(window32(W.bits, L - 32 - 32 * m)) : 0u;
+    }
+    // the entries of the near-peak list that can reach a neighbour's PSL (|C_k| >= PSL - 8:
+    // a flip moves C_k by at most 4, and every neighbour's PSL is at least PSL - 4), once per
+    // item instead of once per position; their order does not matter to a maximum
+    const bool on = W.ktau_on != 0;
+    if (on) {
+      const int nk = (int)W.nktau, floor_c = W.psl - 8;
+      for (int q = (int)threadIdx.x; q < nk; q += NT) {
+        const int2 e = W.ktau[q];
+        if ((e.y < 0 ? -e.y : e.y) >= floor_c) {
+          const int at = atomicAdd(&sm.npeak, 1);
+          if (at < kA2PeakCap) sm.peak[at] = e;
+        }
+      }
+    }
     // planes and in-word prefix sums of C_k, one word of 32 shifts per warp at a time
+    uint32_t *plane_w = reinterpret_cast<uint32_t *>(sm.plane);  // [plane][word]
     for (int w = warp; w < nw; w += NW) {
       const int k = 1 + 32 * w + lane;
       const int c = k < L ? W.C[k] : 0;
-      uint32_t pl[16];
+      uint32_t mine = 0u;  // lane p keeps plane p of this word
 #pragma unroll
-      for (int p = 0; p < 16; p++) pl[p] = p < P ? __ballot_sync(0xffffffffu, (c >> p) & 1) : 0u;
-      if (lane == 0) sm.plane[w][0] = make_uint4(pl[0], pl[1], pl[2], pl[3]);
-      if (lane == 1) sm.plane[w][1] = make_uint4(pl[4], pl[5], pl[6], pl[7]);
-      if (lane == 2) sm.plane[w][2] = make_uint4(pl[8], pl[9], pl[10], pl[11]);
-      if (lane == 3) sm.plane[w][3] = make_uint4(pl[12], pl[13], pl[14], pl[15]);
+      for (int p = 0; p < kA2MaxPlanes; p++) {
+        if (p < P) {  // the same for every lane
+          const uint32_t b = __ballot_sync(0xffffffffu, (c >> p) & 1);
+          if (lane == p) mine = b;
+        }
+      }
+      if (lane < P) plane_w[lane * kA2Words + w] = mine;
       int v = c;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -168,19 +265,27 @@ __global__ void __launch_bounds__(NT) k_hot_alpha2(WalkDev *hdr, const HotItem *
     const int i = (int)it.i0 + (int)threadIdx.x;  // window position, 1-based
     if (i > N) continue;
     const int j = (int)(((uint64_t)W.start + (uint64_t)i) % (uint64_t)L);
-    int dF;
-    if (P <= 4)
-      dF = a2_delta<1>(sm, W, j, L, P);
-    else if (P <= 8)
-      dF = a2_delta<2>(sm, W, j, L, P);
-    else if (P <= 12)
-      dF = a2_delta<3>(sm, W, j, L, P);
-    else
-      dF = a2_delta<4>(sm, W, j, L, P);
+    const int dF = a2_delta_any(sm, W, j, L, P);
     W.score[i - 1] = ldexpf((float)dF, -2 * (int)W.e);  // the tables' scale 2^(-alpha e)
     // exact neighbour PSL, only when some neighbour may beat psl_best
     int pj = INT_MAX;
-    if (W.ktau_on) pj = neighbour_psl(W, W.ktau, (int)W.nktau, j, L, getbit(W.bits, j) ? -1 : 1, W.psl - 8, 0);
+    if (on) {
+      const int sj = ((sm.xs[j >> 5] >> (j & 31)) & 1u) ? -1 : 1;
+      if (sm.npeak <= kA2PeakCap) {
+        pj = 0;
+        for (int q = 0; q < sm.npeak; q++) {
+          const int2 e = sm.peak[q];
+          const int k = e.x;
+          int part = 0;
+          if (j + k < L) part += 1 - 2 * (int)((sm.xs[(j + k) >> 5] >> ((j + k) & 31)) & 1u);
+          if (j >= k) part += 1 - 2 * (int)((sm.xs[(j - k) >> 5] >> ((j - k) & 31)) & 1u);
+          const int cn = e.y - 2 * sj * part;
+          pj = max(pj, cn < 0 ? -cn : cn);
+        }
+      } else {
+        pj = neighbour_psl(W, W.ktau, (int)W.nktau, j, L, sj, W.psl - 8, 0);
+      }
+    }
     W.pslj[i - 1] = pj;
   }
 }

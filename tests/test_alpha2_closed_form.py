@@ -64,6 +64,11 @@ def bit_planes(s):
     def xbit(i):
         return x[i] if 0 <= i < L else 0
 
+    r = [x[L - 1 - i] for i in range(L)]  # the reversed bits: backward partners read forward
+
+    def rbit(i):
+        return r[i] if 0 <= i < L else 0
+
     out = []
     for j in range(L):
         kplus, kin = L - 1 - j, min(j, L - 1 - j)
@@ -71,6 +76,7 @@ def bit_planes(s):
         for w in range(nw):
             fw = sum(xbit(j + 1 + 32 * w + t) << t for t in range(32))  # bit t: x_{j+k}, k = 1 + 32w + t
             rw = sum(xbit(j - 1 - 32 * w - t) << t for t in range(32))  # bit t: x_{j-k}
+            assert rw == sum(rbit(L - j + 32 * w + t) << t for t in range(32))  # = r from L - j
             for p in range(P):
                 sx += wt[p] * bin(planes[w][p] & fw).count("1")
                 sy += wt[p] * bin(planes[w][p] & rw).count("1")
@@ -119,3 +125,34 @@ def test_barker13_is_a_local_optimum():
     s = np.array([1, 1, 1, 1, 1, -1, -1, 1, 1, -1, 1, -1, 1])
     assert energy(s) == 6
     assert min(closed_form(s)) > 0
+
+
+def _fa(a, b, c):
+    """Full adder over 32-bit slices: (sum, carry)."""
+    return a ^ b ^ c, ((a & b) | (c & (a ^ b))) & 0xFFFFFFFF
+
+
+def csa_count(words):
+    """The kernel's carry-save count of the set bits of a list of 32-bit words: four words at a
+    time into (ones, twos), the carries into the fours column counted per group; a short last
+    group reads zero words."""
+    ones = twos = fours = 0
+    pad = words + [0] * (-len(words) % 4)
+    for g in range(0, len(pad), 4):
+        s1, c1 = _fa(ones, pad[g], pad[g + 1])
+        s2, c2 = _fa(s1, pad[g + 2], pad[g + 3])
+        ones = s2
+        s4, c4 = _fa(twos, c1, c2)
+        twos = s4
+        fours += bin(c4).count("1")
+    return bin(ones).count("1") + 2 * bin(twos).count("1") + 4 * fours
+
+
+@pytest.mark.parametrize("n", [0, 1, 3, 4, 5, 8, 31, 32, 33, 128])
+def test_carry_save_count_matches_popcount(n):
+    rng = np.random.default_rng(n)
+    for dense in (False, True):
+        words = [int(w) for w in rng.integers(0, 1 << 32, size=n, dtype=np.uint64)]
+        if dense:
+            words = [0xFFFFFFFF] * n  # every column carries
+        assert csa_count(words) == sum(bin(w).count("1") for w in words)
