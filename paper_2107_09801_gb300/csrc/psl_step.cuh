@@ -31,7 +31,13 @@ __device__ __forceinline__ void apply_finish(WalkDev &W, uint32_t chunk, uint32_
   __shared__ float s_sum[8];
   __shared__ uint32_t s_F[NEED_F ? 256 / 32 : 1][kWideLimbs];
   __shared__ uint32_t s_last, s_fcopy;
+  __shared__ int s_bm;            // the block's own totals, when it covers the whole walk
+  __shared__ float s_bs;
+  __shared__ uint32_t s_bF[kWideLimbs];
   constexpr bool need_F = NEED_F;
+  // one block covers the walk (one update chunk): it is the last to arrive, and hands its
+  // totals to the finalisation directly instead of through the partial records
+  const bool single = W.nchunk_apply == 1u;
   const int L = (int)W.L;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   pmax = warp_max(pmax);
@@ -66,16 +72,23 @@ __device__ __forceinline__ void apply_finish(WalkDev &W, uint32_t chunk, uint32_
         wide_add(Fb, t);
       }
     }
-    part[0] = (uint32_t)m;
-    part[1] = __float_as_uint(s);
-    wide_store(part + 2, Fb);
-    __threadfence();
-    const uint32_t prev = atomicAdd(&W.arrive, 1u);
-    s_last = (prev == W.nchunk_apply - 1u);
+    if (single) {
+      s_bm = m;
+      s_bs = s;
+      wide_store(s_bF, Fb);
+      s_last = 1;
+    } else {
+      part[0] = (uint32_t)m;
+      part[1] = __float_as_uint(s);
+      wide_store(part + 2, Fb);
+      __threadfence();
+      const uint32_t prev = atomicAdd(&W.arrive, 1u);
+      s_last = (prev == W.nchunk_apply - 1u);
+    }
   }
   __syncthreads();
   if (!s_last) return;
-  __threadfence();
+  if (!single) __threadfence();
 
   // ---------------- finalise (last block of this walk) ----------------
   const int nw = (int)W.nw;
@@ -113,14 +126,20 @@ __device__ __forceinline__ void apply_finish(WalkDev &W, uint32_t chunk, uint32_
     float s = 0.f;
     uint32_t Fs[kWideLimbs];
     wide_zero(Fs);
-    for (uint32_t c = 0; c < W.nchunk_apply; c++) {
-      const uint32_t *p = W.ap_part + (size_t)c * kApplyPartStride;
-      m = max(m, (int)__ldcg(p));
-      s += __uint_as_float(__ldcg(p + 1));
-      if (need_F) {
-        uint32_t t[kWideLimbs];
-        wide_load_cg(t, p + 2);
-        wide_add(Fs, t);
+    if (single) {
+      m = s_bm;
+      s = s_bs;
+      if (need_F) wide_load(Fs, s_bF);
+    } else {
+      for (uint32_t c = 0; c < W.nchunk_apply; c++) {
+        const uint32_t *p = W.ap_part + (size_t)c * kApplyPartStride;
+        m = max(m, (int)__ldcg(p));
+        s += __uint_as_float(__ldcg(p + 1));
+        if (need_F) {
+          uint32_t t[kWideLimbs];
+          wide_load_cg(t, p + 2);
+          wide_add(Fs, t);
+        }
       }
     }
     W.psl = m;
@@ -792,12 +811,16 @@ __device__ __forceinline__ void recheck_one(WalkDev &W, uint32_t chunk, uint32_t
         default: recheck_body<16, SHORT, PATH>(W, s_hist, j, kbeg, kend, pos, neg); break;
       }
     }
+    // the sums fill nl limbs (the accumulator width chosen from alpha e + 20 above): only
+    // those travel through the shuffles
+    const int bits = (int)W.alpha * (int)W.e + 20;
+    const int nl = bits <= 128 ? 4 : (bits <= 256 ? 8 : kWideLimbs);
     for (int o = 16; o > 0; o >>= 1) {
       uint32_t a[kWideLimbs], b[kWideLimbs];
 #pragma unroll
       for (int t = 0; t < kWideLimbs; t++) {
-        a[t] = __shfl_down_sync(0xffffffffu, pos[t], o);
-        b[t] = __shfl_down_sync(0xffffffffu, neg[t], o);
+        a[t] = t < nl ? __shfl_down_sync(0xffffffffu, pos[t], o) : 0u;  // nl is the same in every lane
+        b[t] = t < nl ? __shfl_down_sync(0xffffffffu, neg[t], o) : 0u;
       }
       if (lane < o) {
         wide_add(pos, a);

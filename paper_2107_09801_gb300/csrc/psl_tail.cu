@@ -21,12 +21,23 @@ namespace psl {
 constexpr int kTailThreads = 64;
 
 __global__ void __launch_bounds__(256, 3) k_step_tail(WalkDev *hdr, const uint32_t *active, Schedule *sched) {
+  // The walk's header lives in shared memory for the whole of its step: the phases below
+  // read and write its fields one after another (one block owns the walk, nothing else runs
+  // on it meanwhile), so a dependent chain of header accesses costs shared-memory latency
+  // instead of L2 latency.  Copied in before, written back after.
+  __shared__ WalkDev sW;
+  static_assert(sizeof(WalkDev) % 8 == 0 && alignof(WalkDev) <= 8, "the header copies in 8-byte words");
+  constexpr int kHdrWords = (int)(sizeof(WalkDev) / 8);
   // the neighbourhood kernel of this step has finished: rearm its work counter
   if (blockIdx.x == 0 && threadIdx.x == 0) sched->hot_next = 0;
   for (uint32_t a = blockIdx.x; a < sched->nactive; a += gridDim.x) {
-    WalkDev &W = hdr[active[a]];
-    __syncthreads();  // the previous walk's shared buffers are free
-    if (W.status != kRunning) continue;  // one reading for the block: nothing below changes it before it is read
+    WalkDev &G = hdr[active[a]];
+    __syncthreads();  // the previous walk's shared buffers and header copy are free
+    if (G.status != kRunning) continue;  // one reading for the block: nothing below changes it before it is read
+    for (int q = (int)threadIdx.x; q < kHdrWords; q += (int)blockDim.x)
+      reinterpret_cast<uint2 *>(&sW)[q] = reinterpret_cast<const uint2 *>(&G)[q];
+    __syncthreads();
+    WalkDev &W = sW;
     if (threadIdx.x < 32) select_warp(W);
     __syncthreads();  // candidates, bound and window PSL are visible to the block
     const uint32_t nslots = min(W.ncand, (uint32_t)kQcap);
@@ -41,6 +52,9 @@ __global__ void __launch_bounds__(256, 3) k_step_tail(WalkDev *hdr, const uint32
       apply_move_dispatch(W, 0);
     else
       apply_one(W, 0);
+    __syncthreads();
+    for (int q = (int)threadIdx.x; q < kHdrWords; q += (int)blockDim.x)
+      reinterpret_cast<uint2 *>(&G)[q] = reinterpret_cast<const uint2 *>(&sW)[q];
   }
 }
 
