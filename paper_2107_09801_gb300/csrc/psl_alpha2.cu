@@ -267,6 +267,7 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_hot_alpha2(WalkDev *hdr, cons
     const int j = (int)(((uint64_t)W.start + (uint64_t)i) % (uint64_t)L);
     const int dF = a2_delta_any(sm, W, j, L, P);
     W.score[i - 1] = ldexpf((float)dF, -2 * (int)W.e);  // the tables' scale 2^(-alpha e)
+    reinterpret_cast<int *>(W.score_part)[i - 1] = dF;   // exact, for the re-check of the candidates
     // exact neighbour PSL, only when some neighbour may beat psl_best
     int pj = INT_MAX;
     if (on) {

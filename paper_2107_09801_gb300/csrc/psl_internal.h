@@ -64,7 +64,8 @@ struct WalkDev {
   int32_t *C, *C_local;
   float4 *T;          // per k: (Tp4, Tm4, Tp2, Tm2), scaled by 2^(-alpha*e)
   float *score;       // FP32 filter score of window position i at [i-1]
-  float *score_part;  // per-k-chunk partial scores [chunk][N] when the k range is split
+  float *score_part;  // per-k-chunk partial scores [chunk][N] when the k range is split; with the
+                      // alpha = 2 closed form (never split) the exact Delta F of each neighbour, as int32
   int32_t *pslj;      // exact neighbour PSL (or INT32_MAX when not needed)
   int2 *ktau;         // near-peak list (k, C_k)
   uint32_t *cand;     // candidate window positions, ascending
@@ -115,7 +116,9 @@ struct Schedule {
   uint32_t hot_next;         // next neighbourhood item to hand out (reset by k_decide)
   uint32_t general;          // some listed walk needs the general update pass (initialisation or a phase
                              // switch): set by the host and by k_decide, cleared by k_select
-  uint32_t pad[2];
+  uint32_t alpha2;           // the batch is scored by the alpha = 2 closed form: every neighbour's exact
+                             // Delta F is in its walk's score_part (as int32), so the re-check copies it
+  uint32_t pad;
 };
 
 struct LaunchCtx {

@@ -18,16 +18,18 @@ template <int PATH>
 __global__ void __launch_bounds__(256, PATH == kRcHist ? 4 : 2) k_recheck(WalkDev *hdr, const uint32_t *active,
                                                                          const Schedule *sched) {
   const uint32_t nch = sched->max_chunk_rc, V = sched->nactive * nch;
+  const bool exact = sched->alpha2 != 0;  // the closed form kept every neighbour's exact Delta F
   for (uint32_t v = blockIdx.x; v < V; v += gridDim.x) {
     WalkDev &W = hdr[active[v / nch]];
     const uint32_t chunk = v % nch;
     if (W.status != kRunning || chunk >= W.nchunk_rc) continue;  // uniform over the block
     if (W.shard_count > 1 && chunk % W.shard_count != W.shard_rank) continue;  // another rank's chunk
-    if (((int)W.e <= kHistLog) != (PATH == kRcHist)) continue;  // the other kernel's walk
+    // the other kernel's walk (the exact copies of the closed form all go to the histogram kernel)
+    if (exact ? PATH != kRcHist : (((int)W.e <= kHistLog) != (PATH == kRcHist))) continue;
     const uint32_t nslots = min(W.ncand, (uint32_t)kQcap);
     for (uint32_t qslot = 0; qslot < nslots; qslot++) {
       __syncthreads();
-      recheck_one<false, PATH>(W, chunk, qslot);
+      recheck_one<false, PATH>(W, chunk, qslot, exact);
     }
   }
 }

@@ -653,6 +653,7 @@ static int rebuild_active(psl_ctx *ctx) {
   sc.max_chunk_rc = ctx->max_chunk_rc;
   sc.hot_next = 0;
   sc.general = 1;
+  sc.alpha2 = ctx->alpha2 ? 1u : 0u;
   CK(xfer(ctx, ctx->d_sched, &sc, sizeof sc, cudaMemcpyHostToDevice));
   CK(cudaStreamSynchronize(ctx->stream));  // h_pinned and sc are reused / temporaries
   ctx->active_dirty = false;

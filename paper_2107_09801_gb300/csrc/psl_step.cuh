@@ -772,12 +772,30 @@ __device__ void recheck_body(WalkDev &W, int *hist, int j, int kbeg, int kend, u
 
 static_assert(kTailMaxL <= 8192u, "the SHORT re-check relies on e <= 14");
 
+// exact: the step was scored by the alpha = 2 closed form, which kept every neighbour's exact
+// Delta F (score_part as int32; such walks have one re-check chunk): the first call copies the
+// candidates' values into their records, sign-extended, and the other calls have nothing to do.
 template <bool SHORT, int PATH>
-__device__ __forceinline__ void recheck_one(WalkDev &W, uint32_t chunk, uint32_t qslot) {
+__device__ __forceinline__ void recheck_one(WalkDev &W, uint32_t chunk, uint32_t qslot, bool exact) {
   __shared__ uint32_t s_w[8][2 * kWideLimbs];
   __shared__ int s_hist[PATH == kRcTerms ? 1 : 1 << (SHORT ? kHistLogShort : kHistLog)];
   if (W.status != kRunning) return;
   if (chunk >= W.nchunk_rc) return;
+  if (exact) {
+    if (qslot != 0 || chunk != 0) return;
+    const int *dF = reinterpret_cast<const int *>(W.score_part);
+    for (uint32_t q = threadIdx.x; q < W.ncand; q += blockDim.x) {
+      const int v = dF[W.cand[q] - 1];
+      uint32_t P[kWideLimbs];
+      P[0] = (uint32_t)v;
+#pragma unroll
+      for (int t = 1; t < kWideLimbs; t++) P[t] = v < 0 ? 0xffffffffu : 0u;
+      const bool whole = q >= (uint32_t)kQcap;
+      const size_t slot = whole ? ((size_t)kQcap * W.nchunk_rc + (q - kQcap)) : ((size_t)q * W.nchunk_rc);
+      wide_store(W.rc_part + slot * kWideLimbs, P);
+    }
+    return;
+  }
   const int L = (int)W.L;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (uint32_t q = qslot; q < W.ncand; q += kQcap) {

@@ -30,6 +30,7 @@ __global__ void __launch_bounds__(256, 3) k_step_tail(WalkDev *hdr, const uint32
   constexpr int kHdrWords = (int)(sizeof(WalkDev) / 8);
   // the neighbourhood kernel of this step has finished: rearm its work counter
   if (blockIdx.x == 0 && threadIdx.x == 0) sched->hot_next = 0;
+  const bool exact = sched->alpha2 != 0;  // the closed form kept every neighbour's exact Delta F
   for (uint32_t a = blockIdx.x; a < sched->nactive; a += gridDim.x) {
     WalkDev &G = hdr[active[a]];
     __syncthreads();  // the previous walk's shared buffers and header copy are free
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(256, 3) k_step_tail(WalkDev *hdr, const uint32
     const uint32_t nslots = min(W.ncand, (uint32_t)kQcap);
     for (uint32_t qslot = 0; qslot < nslots; qslot++) {
       __syncthreads();
-      recheck_one<true, kRcBoth>(W, 0, qslot);
+      recheck_one<true, kRcBoth>(W, 0, qslot, exact);
     }
     __syncthreads();  // re-check partials are visible
     decide_one(W);
