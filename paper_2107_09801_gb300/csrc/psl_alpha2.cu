@@ -262,32 +262,36 @@ __global__ void __launch_bounds__(NT, 1024 / NT) k_hot_alpha2(WalkDev *hdr, cons
       }
     }
     __syncthreads();
-    const int i = (int)it.i0 + (int)threadIdx.x;  // window position, 1-based
-    if (i > N) continue;
-    const int j = (int)(((uint64_t)W.start + (uint64_t)i) % (uint64_t)L);
-    const int dF = a2_delta_any(sm, W, j, L, P);
-    W.score[i - 1] = ldexpf((float)dF, -2 * (int)W.e);  // the tables' scale 2^(-alpha e)
-    reinterpret_cast<int *>(W.score_part)[i - 1] = dF;   // exact, for the re-check of the candidates
-    // exact neighbour PSL, only when some neighbour may beat psl_best
-    int pj = INT_MAX;
-    if (on) {
-      const int sj = ((sm.xs[j >> 5] >> (j & 31)) & 1u) ? -1 : 1;
-      if (sm.npeak <= kA2PeakCap) {
-        pj = 0;
-        for (int q = 0; q < sm.npeak; q++) {
-          const int2 e = sm.peak[q];
-          const int k = e.x;
-          int part = 0;
-          if (j + k < L) part += 1 - 2 * (int)((sm.xs[(j + k) >> 5] >> ((j + k) & 31)) & 1u);
-          if (j >= k) part += 1 - 2 * (int)((sm.xs[(j - k) >> 5] >> ((j - k) & 31)) & 1u);
-          const int cn = e.y - 2 * sj * part;
-          pj = max(pj, cn < 0 ? -cn : cn);
+    // kA2PerThread window positions per thread, NT apart: an item's planes, sums and bit arrays
+    // serve kA2PerThread x NT positions (every position does the same work)
+    for (int r = 0; r < (int)kA2PerThread; r++) {
+      const int i = (int)it.i0 + (int)threadIdx.x + r * NT;  // window position, 1-based
+      if (i > N) break;
+      const int j = (int)(((uint64_t)W.start + (uint64_t)i) % (uint64_t)L);
+      const int dF = a2_delta_any(sm, W, j, L, P);
+      W.score[i - 1] = ldexpf((float)dF, -2 * (int)W.e);  // the tables' scale 2^(-alpha e)
+      reinterpret_cast<int *>(W.score_part)[i - 1] = dF;   // exact, for the re-check of the candidates
+      // exact neighbour PSL, only when some neighbour may beat psl_best
+      int pj = INT_MAX;
+      if (on) {
+        const int sj = ((sm.xs[j >> 5] >> (j & 31)) & 1u) ? -1 : 1;
+        if (sm.npeak <= kA2PeakCap) {
+          pj = 0;
+          for (int q = 0; q < sm.npeak; q++) {
+            const int2 e = sm.peak[q];
+            const int k = e.x;
+            int part = 0;
+            if (j + k < L) part += 1 - 2 * (int)((sm.xs[(j + k) >> 5] >> ((j + k) & 31)) & 1u);
+            if (j >= k) part += 1 - 2 * (int)((sm.xs[(j - k) >> 5] >> ((j - k) & 31)) & 1u);
+            const int cn = e.y - 2 * sj * part;
+            pj = max(pj, cn < 0 ? -cn : cn);
+          }
+        } else {
+          pj = neighbour_psl(W, W.ktau, (int)W.nktau, j, L, sj, W.psl - 8, 0);
         }
-      } else {
-        pj = neighbour_psl(W, W.ktau, (int)W.nktau, j, L, sj, W.psl - 8, 0);
       }
+      W.pslj[i - 1] = pj;
     }
-    W.pslj[i - 1] = pj;
   }
 }
 

@@ -160,6 +160,8 @@ cudaError_t launch_recheck(const LaunchCtx &c);
 cudaError_t launch_decide(const LaunchCtx &c);
 cudaError_t launch_step_tail(const LaunchCtx &c);  // select..apply in one kernel, short walks only
 constexpr uint32_t kA2MaxL = 4095;  // walks up to this length can take the alpha = 2 closed form
+constexpr uint32_t kA2PerThread = 4;  // window positions per thread of the closed-form kernel (per work item:
+                                      // this many times the block size)
 constexpr uint32_t kTailMaxL = kApplyChunk;      // walks up to this length (one update chunk, one re-check chunk)
 constexpr uint32_t kTailMaxN = 2048;             // and windows up to this size (one warp selects)
 cudaError_t launch_start_init(const LaunchCtx &c);

@@ -606,7 +606,7 @@ static int rebuild_active(psl_ctx *ctx) {
   }
   // Split every walk's k range into chunks when the neighbour blocks alone would leave
   // SMs idle (few walks, or a long walk on its own): aim for about four blocks per SM.
-  const uint32_t T_ = (uint32_t)ctx->cfg.hot_threads;
+  const uint32_t T_ = (uint32_t)ctx->cfg.hot_threads * (a2 ? kA2PerThread : 1u);  // window positions per item
   uint64_t nblocks = 0;
   for (uint32_t s : ctx->active) nblocks += (ctx->h_hdr[s].N + T_ - 1) / T_;
   const uint64_t target = 4ull * (uint64_t)ctx->sm_count;
