@@ -16,11 +16,12 @@ namespace psl {
 // launches of latency-bound kernels
 // ------------------------------------------------------------------------------------
 // Blocks of two warps: each walk's chain of phases is bound by latency, so the more walks
-// an SM holds at once the better (64 threads: 12 blocks per SM, against 3 of 256 threads;
-// measured at L = 1023 x 4096: 0.108 against 0.230 ms per step).
+// an SM holds at once the better (64 threads: 12 blocks per SM at 80 registers, against 3 of
+// 256 threads, measured at L = 1023 x 4096: 0.108 against 0.230 ms per step; 16 blocks at
+// 64 registers, with a few bytes of spills: 0.074 against 0.067 ms).
 constexpr int kTailThreads = 64;
 
-__global__ void __launch_bounds__(256, 3) k_step_tail(WalkDev *hdr, const uint32_t *active, Schedule *sched) {
+__global__ void __launch_bounds__(64, 16) k_step_tail(WalkDev *hdr, const uint32_t *active, Schedule *sched) {
   // The walk's header lives in shared memory for the whole of its step: the phases below
   // read and write its fields one after another (one block owns the walk, nothing else runs
   // on it meanwhile), so a dependent chain of header accesses costs shared-memory latency
