@@ -106,11 +106,12 @@ __device__ __forceinline__ void apply_finish(WalkDev &W, uint32_t chunk, uint32_
   // partner windows of the new pivot: one move changes 32 entries of each, any other pivot
   // (the start, a perturbed local_best) is rebuilt whole
   if (mode == kModeMove) {
-    const int t = (int)threadIdx.x;
-    if (t < 32)
-      W.win_f[kstar - t] ^= 1u << t;  // s_{p+t} with p + t = k*
-    else if (t < 64)
-      W.win_r[kstar + (t - 32)] ^= 1u << (t - 32);  // s_{p-t} with p - t = k*
+    for (int t = (int)threadIdx.x; t < 64; t += (int)blockDim.x) {  // any block size
+      if (t < 32)
+        W.win_f[kstar - t] ^= 1u << t;  // s_{p+t} with p + t = k*
+      else
+        W.win_r[kstar + (t - 32)] ^= 1u << (t - 32);  // s_{p-t} with p - t = k*
+    }
   } else {
     for (int p = (int)threadIdx.x - kWinGuard; p < L + kWinGuard; p += blockDim.x) {
       W.win_f[p] = window32(W.bits, p);

@@ -15,11 +15,13 @@ namespace psl {
 // runs selection, exact re-check, decision and update back to back, instead of four
 // launches of latency-bound kernels
 // ------------------------------------------------------------------------------------
-// Blocks of two warps: each walk's chain of phases is bound by latency, so the more walks
-// an SM holds at once the better (64 threads: 12 blocks per SM at 80 registers, against 3 of
-// 256 threads, measured at L = 1023 x 4096: 0.108 against 0.230 ms per step; 16 blocks at
-// 64 registers, with a few bytes of spills: 0.074 against 0.067 ms).
-constexpr int kTailThreads = 64;
+// Blocks of one warp: each walk's chain of phases is bound by latency, so the more walks an
+// SM holds at once the better.  Measured at L = 1023 x 4096: 256 threads, 3 blocks per SM
+// 0.230 ms per step; 64 threads at 80 registers, 12 blocks 0.108 ms (then, after the shared
+// header copy, 0.074 ms); 64 registers, 16 blocks 0.067 ms; one warp, 32 blocks 0.063 ms.
+// (The register bound stays that of 64-thread blocks: bounding for 32-thread blocks makes
+// the compiler spill a kilobyte.)  Every phase below is written for any block size.
+constexpr int kTailThreads = 32;
 
 __global__ void __launch_bounds__(64, 16) k_step_tail(WalkDev *hdr, const uint32_t *active, Schedule *sched) {
   // The walk's header lives in shared memory for the whole of its step: the phases below
