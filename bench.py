@@ -18,6 +18,7 @@ import argparse
 import dataclasses
 import csv
 import hashlib
+import re
 import io
 import json
 import os
@@ -219,13 +220,22 @@ def run_reference(args):
 # ------------------------------------------------------------------------------------------------
 # our arm
 # ------------------------------------------------------------------------------------------------
+def _code_only(src: str) -> str:
+    """C++ source without comments and blank lines (string literals here hold no comment
+    markers), so that the hash follows the code the counters were measured on."""
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", "", src)
+    return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+
+
 def kernel_source_hash(kernel: str = "k_hot_batched") -> str:
-    """Hash of the sources of a neighbourhood kernel (its translation unit and headers)."""
+    """Hash of the code of a neighbourhood kernel (its translation unit and device header,
+    comments left out)."""
     h = hashlib.sha256()
     tu = "psl_alpha2.cu" if kernel.startswith("k_hot_alpha2") else "psl_hot.cu"
     for fn in (tu, "psl_device.cuh"):
-        with open(os.path.join(ROOT, "paper_2107_09801_gb300", "csrc", fn), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, "paper_2107_09801_gb300", "csrc", fn), encoding="utf-8") as f:
+            h.update(_code_only(f.read()).encode())
     return h.hexdigest()[:16]
 
 

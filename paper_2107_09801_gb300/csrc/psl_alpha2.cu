@@ -15,11 +15,12 @@
 // is at least 72 2^-24 S_abs >= 72 2^-24 |Delta F|), so selection, re-check and decision run
 // unchanged.
 //
-// A block takes work items (up to NT window positions of one walk) from the schedule, builds the
-// walk's planes and prefix sums of C in shared memory, and scores one position per thread.
-// Every position covers about (L-1)/32 words whatever its place in the sequence (the forward
-// and backward ranges add up to L - 1), so the warps of a block do equal work and no block
-// waits on another.
+// A block takes work items (up to kA2PerThread x NT window positions of one walk) from the
+// schedule, builds the walk's planes, prefix sums of C, bit arrays and near-peak entries in
+// shared memory, and scores kA2PerThread positions per thread, NT apart.  Every position
+// covers about (L-1)/32 words whatever its place in the sequence (the forward and backward
+// ranges add up to L - 1), so the warps of a block do equal work and no block waits on
+// another.
 #include <climits>
 #include <cstdint>
 #include <cstdio>

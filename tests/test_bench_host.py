@@ -75,7 +75,10 @@ def test_stored_counters_only_for_the_current_source(tmp_path, monkeypatch):
     assert bench.stored_counters("k_hot_pc<28,32,8>", "W")["bytes_per_launch"] == 1
     assert bench.stored_counters("k_hot_alpha2<256>", "W") is None  # taken on another source
     assert bench.stored_counters("k_hot_pc<28,32,8>", "other") is None
-    # a change to the kernel's translation unit invalidates its counters
+    # a comment or a blank line leaves the counters valid; a change to the code does not
     with open(csrc / "psl_hot.cu", "a") as f:
-        f.write("\n")
+        f.write("\n// a remark\n\n/* another */\n")
+    assert bench.stored_counters("k_hot_pc<28,32,8>", "W")["bytes_per_launch"] == 1
+    with open(csrc / "psl_hot.cu", "a") as f:
+        f.write("static int unused_probe_value;\n")
     assert bench.stored_counters("k_hot_pc<28,32,8>", "W") is None
