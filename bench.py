@@ -239,6 +239,17 @@ def kernel_source_hash(kernel: str = "k_hot_batched") -> str:
     return h.hexdigest()[:16]
 
 
+KERNELS_PER_PHASE = {"hot": 1, "select": 1, "recheck": 2, "decide": 1, "apply": 2, "tail": 1}
+
+
+def kernels_per_step(breakdown: dict) -> int:
+    """Kernel launches of one step from a per-phase breakdown of whole steps (a phase's
+    launches count its brackets, one per step)."""
+    steps = max(breakdown.get("hot", (0, 0.0))[0], 1)
+    total = sum(KERNELS_PER_PHASE.get(k, 1) * n for k, (n, _) in breakdown.items() if n)
+    return int(round(total / steps))
+
+
 def plane_steps_per_flip_eval(L: int, psls) -> float:
     """Bit-plane steps (logic op, population count, add) of the alpha = 2 closed form per
     flip-eval, averaged over the neighbour position: P = bitlen(PSL) + 1 planes for each of the
@@ -494,9 +505,11 @@ def run_ours(args):
                         psls)
     roof["hot_launches_timed"] = n_hot
     kernels = {k: {"launches": n, "avg_ms": (ms_ / n if n else 0.0)} for k, (n, ms_) in breakdown.items() if n}
-    # kernels per step: the neighbourhood score, then either one fused kernel (short walks) or
-    # select, re-check, decide and the two update passes (ordinary moves; initialisation/switch)
-    launches = args.steps * (2 if breakdown.get("tail", (0, 0.0))[0] else 6)
+    # kernels per step, from the untimed breakdown (each profiled phase brackets its kernels):
+    # the neighbourhood score, then either the fused tail (short walks) or select, the two
+    # re-check kernels (histogram / term sums), decide and the two update passes (ordinary
+    # moves; initialisation and switches)
+    launches = args.steps * kernels_per_step(breakdown)
 
     # plain form: one walk per launch, one thread per neighbour, host-side selection
     plain = None

@@ -82,3 +82,11 @@ def test_stored_counters_only_for_the_current_source(tmp_path, monkeypatch):
     with open(csrc / "psl_hot.cu", "a") as f:
         f.write("static int unused_probe_value;\n")
     assert bench.stored_counters("k_hot_pc<28,32,8>", "W") is None
+
+
+def test_kernels_per_step():
+    # two profiled steps: the general path launches seven kernels a step, the fused tail two
+    general = {"hot": (2, 1.0), "select": (2, 0.1), "recheck": (2, 0.1), "decide": (2, 0.1), "apply": (2, 0.1)}
+    assert bench.kernels_per_step(general) == 7
+    assert bench.kernels_per_step({"hot": (2, 1.0), "tail": (2, 0.1)}) == 2
+    assert bench.kernels_per_step({"hot": (2, 1.0)}) == 1
