@@ -2,18 +2,20 @@
 // Boskovic and Brest, "Two-phase Optimization of Binary Sequences with Low Peak
 // Sidelobe Level Value" (arXiv 2107.09801).
 //
-// One walk step (the body of the while loop of Algorithm 1) is five kernels:
+// One walk step (the body of the while loop of Algorithm 1) is five phases:
 //   hot     FP32 filter score of every neighbour in the window (Eq. 4 through the
 //           one-element flip of Sec. 3) and, when it can matter, its exact PSL (Eq. 3)
-//           -- in psl_hot.cu
+//           -- psl_hot.cu (subset-sum tables), psl_alpha2.cu (the closed form at alpha = 2)
 //   select  minimum score, the certified candidate set {score <= min + 2B} plus the
 //           FP32 top-k, and the first neighbour of minimum PSL
-//   recheck exact 384-bit Delta F of every candidate
+//   recheck exact Delta F of every candidate -- psl_recheck.cu (two kernels)
 //   decide  exact argmin (first in scan order), bookkeeping and phase switch of Alg. 1
-//   apply   O(L) update of C, PSL, the next step's per-k tables and near-peak list
-// This file holds the walk initialisation and the last four.  Work shared between blocks
-// of a walk ends in a "last block to arrive finishes the walk" counter: no block here
-// waits on another.
+//   apply   O(L) update of C, PSL, the next step's per-k tables and near-peak list (two
+//           kernels: ordinary moves, and initialisation / phase switches)
+// For batches of short walks select..apply run as one kernel (psl_tail.cu).  This file
+// holds the walk initialisation, select, decide and apply.  Work shared between blocks of
+// a walk ends in a "last block to arrive finishes the walk" counter: no block here waits
+// on another.
 #include <cfloat>
 #include <climits>
 #include <cstdint>

@@ -799,7 +799,7 @@ static int capture_graph(psl_ctx *ctx) {
   drop_graph(ctx);
   const uint32_t G = (uint32_t)ctx->cfg.steps_per_graph;
   LaunchCtx c = launch_ctx(ctx, ctx->d_active, ctx->d_sched);
-  if (ctx->prof) CK(gprof_reserve(ctx, (size_t)G * 5));  // at most five kernels a step
+  if (ctx->prof) CK(gprof_reserve(ctx, (size_t)G * 5));  // at most five profiled phases a step
   cudaGraph_t g;
   CK(cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
   cudaError_t e = cudaSuccess;
